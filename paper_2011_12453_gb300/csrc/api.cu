@@ -1,0 +1,336 @@
+// C ABI entry points of libgna.so: argument validation, workspace carving and dispatch
+// to the kernels.  Every check here runs on the host before anything is enqueued.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace gna {
+
+static thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+void set_last_cuda_error(cudaError_t e) { t_last_cuda_error = e; }
+
+gna_status device_info(DeviceInfo* out) {
+  static std::mutex mu;
+  static DeviceInfo cache[64];
+  static bool have[64] = {false};
+  int dev = 0;
+  GNA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GNA_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!have[dev]) {
+    DeviceInfo di;
+    GNA_CUDA_TRY(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
+    GNA_CUDA_TRY(cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int major = 0, minor = 0;
+    GNA_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    GNA_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    di.cc = major * 10 + minor;
+    cache[dev] = di;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return GNA_OK;
+}
+
+static bool desc_ok(const gna_model_desc* d) {
+  if (!d) return false;
+  if (d->F < 1 || d->F > kMaxF) return false;
+  if (d->L < 0 || d->L > kMaxL) return false;
+  if (d->act != GNA_ACT_TANH) return false;
+  if (d->prec < GNA_PREC_FP64 || d->prec > GNA_PREC_BF16) return false;
+  if (d->shared_weights != 0 && d->shared_weights != 1) return false;
+  if (d->prec == GNA_PREC_BF16 && d->F % 16 != 0) return false;
+  return true;
+}
+
+static gna_status check_gd(const gna_graph* g, const gna_model_desc* d) {
+  if (!g || !desc_ok(d)) return GNA_ERR_INVALID_ARG;
+  if (d->L > g->d.Lmax) return GNA_ERR_INVALID_ARG;
+  int dev = 0;
+  GNA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != g->device) return GNA_ERR_INVALID_ARG;
+  return GNA_OK;
+}
+
+// Arithmetic of the SIMT kernels for a descriptor: BF16 descriptors run their
+// non-tensor-core steps (sampler, backward) in float32.
+static int simt_prec(const gna_model_desc* d) { return d->prec == GNA_PREC_FP64 ? GNA_PREC_FP64 : GNA_PREC_FP32; }
+
+static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int op, int64_t B, size_t* bytes);
+
+}  // namespace gna
+
+using namespace gna;
+
+extern "C" int32_t gna_version(void) { return 1; }
+
+extern "C" const char* gna_status_string(gna_status s) {
+  switch (s) {
+    case GNA_OK:
+      return "ok";
+    case GNA_ERR_INVALID_ARG:
+      return "invalid argument";
+    case GNA_ERR_CUDA:
+      return cudaGetErrorString(t_last_cuda_error);
+    case GNA_ERR_TIMEOUT:
+      return "a bounded device-side wait timed out";
+    case GNA_ERR_NONFINITE:
+      return "non-finite value";
+    case GNA_ERR_WORKSPACE:
+      return "workspace too small";
+    case GNA_ERR_UNSUPPORTED:
+      return "unsupported by this build";
+    case GNA_WARN_DEGENERATE_WEIGHTS:
+      return "degenerate importance weights";
+  }
+  return "unknown status";
+}
+
+extern "C" gna_status gna_model_desc_init(gna_model_desc* d, int32_t F, int32_t L, int32_t act, int32_t prec,
+                                          int32_t shared_weights) {
+  if (!d) return GNA_ERR_INVALID_ARG;
+  gna_model_desc t{F, L, act, prec, shared_weights};
+  if (!desc_ok(&t)) return GNA_ERR_INVALID_ARG;
+  *d = t;
+  return GNA_OK;
+}
+
+extern "C" int64_t gna_num_params(const gna_model_desc* d) {
+  if (!desc_ok(d)) return -1;
+  const int64_t F = d->F;
+  const int64_t nl = d->shared_weights ? 1 : d->L;
+  return 3 * F + nl * (2 * F * F + F) + (F + 2) * 2 + 2;
+}
+
+namespace gna {
+
+static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int op, int64_t B, size_t* bytes) {
+  const Dims m = make_dims(g, d);
+  const int sp = simt_prec(d);
+  switch (op) {
+    case GNA_OP_FORWARD:
+      if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_FWD, B, bytes);
+      return simt_workspace(g, m, sp, 0, B, bytes);
+    case GNA_OP_LOCAL_ENERGY_FULL:
+      return simt_workspace(g, m, sp, 1, B, bytes);
+    case GNA_OP_LOCAL_ENERGY_INCREMENTAL:
+      if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_ELOC, B, bytes);
+      return simt_workspace(g, m, sp, 2, B, bytes);
+    case GNA_OP_METROPOLIS:
+      return simt_workspace(g, m, sp, 3, B, bytes);
+    case GNA_OP_BACKWARD:
+      return simt_workspace(g, m, sp, 4, B, bytes);
+    case GNA_OP_ISGO_WEIGHTS:
+      *bytes = isgo_weights_ws(B);
+      return GNA_OK;
+    case GNA_OP_ISGO_GRAD: {
+      size_t a = 0, b = 0, c = 0;
+      gna_status st = op_workspace(g, d, GNA_OP_FORWARD, B, &a);
+      if (st != GNA_OK) return st;
+      st = op_workspace(g, d, GNA_OP_LOCAL_ENERGY_INCREMENTAL, B, &b);
+      if (st != GNA_OK) return st;
+      st = op_workspace(g, d, GNA_OP_BACKWARD, B, &c);
+      if (st != GNA_OK) return st;
+      size_t inner = a > b ? a : b;
+      inner = inner > c ? inner : c;
+      inner = inner > isgo_weights_ws(B) ? inner : isgo_weights_ws(B);
+      *bytes = 3 * align_up((size_t)B * 2 * sizeof(double)) + inner;
+      return GNA_OK;
+    }
+  }
+  return GNA_ERR_INVALID_ARG;
+}
+
+static gna_status check_ws(const gna_graph* g, const gna_model_desc* d, int op, int64_t B, void* ws, size_t bytes) {
+  size_t need = 0;
+  gna_status st = op_workspace(g, d, op, B, &need);
+  if (st != GNA_OK) return st;
+  if (bytes < need || (need > 0 && ws == nullptr)) return GNA_ERR_WORKSPACE;
+  return GNA_OK;
+}
+
+}  // namespace gna
+
+extern "C" gna_status gna_workspace_size(const gna_graph* g, const gna_model_desc* d, int32_t op, int64_t B,
+                                         size_t* bytes) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (!bytes || B < 0) return GNA_ERR_INVALID_ARG;
+  return op_workspace(g, d, op, B, bytes);
+}
+
+extern "C" gna_status gna_forward(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                  const int8_t* spins, int64_t B, double* logpsi, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (B == 0) return GNA_OK;
+  if (!theta || !spins || !logpsi) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, GNA_OP_FORWARD, B, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  const Dims m = make_dims(g, d);
+  if (d->prec == GNA_PREC_BF16) {
+    TcCall tc{g, m, TC_FWD, (const float*)theta, spins, B, logpsi, nullptr, nullptr};
+    return tc_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
+  SimtCall sc{};
+  sc.g = g;
+  sc.m = m;
+  sc.op = 0;
+  sc.theta = theta;
+  sc.spins = spins;
+  sc.B = B;
+  sc.logpsi = logpsi;
+  return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_local_energy(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                       const int8_t* spins, int64_t B, int32_t mode, double* eloc,
+                                       float* dlogpsi_bonds, void* workspace, size_t workspace_bytes,
+                                       void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (mode != GNA_ELOC_FULL && mode != GNA_ELOC_INCREMENTAL) return GNA_ERR_INVALID_ARG;
+  if (B == 0) return GNA_OK;
+  if (!theta || !spins || !eloc) return GNA_ERR_INVALID_ARG;
+  const int op = mode == GNA_ELOC_FULL ? GNA_OP_LOCAL_ENERGY_FULL : GNA_OP_LOCAL_ENERGY_INCREMENTAL;
+  st = check_ws(g, d, op, B, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  const Dims m = make_dims(g, d);
+  if (d->prec == GNA_PREC_BF16 && mode == GNA_ELOC_INCREMENTAL) {
+    TcCall tc{g, m, TC_ELOC, (const float*)theta, spins, B, nullptr, eloc, dlogpsi_bonds};
+    return tc_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
+  SimtCall sc{};
+  sc.g = g;
+  sc.m = m;
+  sc.op = mode == GNA_ELOC_FULL ? 1 : 2;
+  sc.theta = theta;
+  sc.spins = spins;
+  sc.B = B;
+  sc.eloc = eloc;
+  sc.dlogpsi = dlogpsi_bonds;
+  return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                           int8_t* chain_spins, int64_t C, int32_t n_sweeps, int32_t record_every,
+                                           uint64_t seed, uint64_t step0, int8_t* samples_out, double* logpsi_out,
+                                           int32_t* n_accepted, double* trace, void* workspace,
+                                           size_t workspace_bytes, void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (C < 0 || C > (int64_t)1 << 31 || n_sweeps < 0 || record_every < 0) return GNA_ERR_INVALID_ARG;
+  if (C == 0 || n_sweeps == 0) return GNA_OK;
+  if (g->d.E < 1) return GNA_ERR_INVALID_ARG;  // no bond to propose
+  if (!theta || !chain_spins) return GNA_ERR_INVALID_ARG;
+  if (record_every > 0 && n_sweeps / record_every > 0 && !samples_out && !logpsi_out) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, GNA_OP_METROPOLIS, C, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  SimtCall sc{};
+  sc.g = g;
+  sc.m = make_dims(g, d);
+  sc.op = 3;
+  sc.theta = theta;
+  sc.B = C;
+  sc.chain_spins = chain_spins;
+  sc.n_sweeps = n_sweeps;
+  sc.record_every = record_every;
+  sc.seed = seed;
+  sc.step0 = step0;
+  sc.samples_out = samples_out;
+  sc.logpsi_out = logpsi_out;
+  sc.n_acc = n_accepted;
+  sc.trace = trace;
+  return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_backward(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                   const int8_t* spins, int64_t B, const double* cot, double* grad, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!theta || !grad || (B > 0 && (!spins || !cot))) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, GNA_OP_BACKWARD, B, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  SimtCall sc{};
+  sc.g = g;
+  sc.m = make_dims(g, d);
+  sc.op = 4;
+  sc.theta = theta;
+  sc.spins = spins;
+  sc.B = B;
+  sc.cot = cot;
+  sc.grad = grad;
+  return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_isgo_weights_workspace(int64_t B, size_t* bytes) {
+  if (!bytes || B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  *bytes = isgo_weights_ws(B);
+  return GNA_OK;
+}
+
+extern "C" gna_status gna_isgo_weights(const double* logpsi, const double* logpsi0, const double* eloc,
+                                       const double* counts, int64_t B, double* cot, double* stats, void* workspace,
+                                       size_t workspace_bytes, void* stream) {
+  if (B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!logpsi || !logpsi0 || !eloc || !stats) return GNA_ERR_INVALID_ARG;
+  if (workspace_bytes < isgo_weights_ws(B) || !workspace) return GNA_ERR_WORKSPACE;
+  return isgo_weights_launch(logpsi, logpsi0, eloc, counts, B, cot, stats, workspace, (cudaStream_t)stream);
+}
+
+extern "C" gna_status isgo_grad(const gna_graph* g, const gna_model_desc* d, const void* theta, const int8_t* spins,
+                                const double* logpsi0, const double* counts, int64_t B, double* grad, double* stats,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!theta || !spins || !logpsi0 || !grad || !stats) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, GNA_OP_ISGO_GRAD, B, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  unsigned char* w = (unsigned char*)workspace;
+  const size_t vec = align_up((size_t)B * 2 * sizeof(double));
+  double* lp = (double*)w;
+  double* E = (double*)(w + vec);
+  double* cot = (double*)(w + 2 * vec);
+  unsigned char* inner = w + 3 * vec;
+  const size_t inner_bytes = workspace_bytes - 3 * vec;
+  st = gna_forward(g, d, theta, spins, B, lp, inner, inner_bytes, stream);
+  if (st != GNA_OK) return st;
+  st = gna_local_energy(g, d, theta, spins, B, GNA_ELOC_INCREMENTAL, E, nullptr, inner, inner_bytes, stream);
+  if (st != GNA_OK) return st;
+  st = isgo_weights_launch(lp, logpsi0, E, counts, B, cot, stats, inner, (cudaStream_t)stream);
+  if (st != GNA_OK) return st;
+  return gna_backward(g, d, theta, spins, B, cot, grad, inner, inner_bytes, stream);
+}
+
+extern "C" gna_status gna_sgd_update(const gna_model_desc* d, void* theta, const double* grad, double lr,
+                                     void* stream) {
+  if (!desc_ok(d) || !theta || !grad || !std::isfinite(lr)) return GNA_ERR_INVALID_ARG;
+  return sgd_launch(d->prec, theta, grad, lr, (int)gna_num_params(d), (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_philox4x64_10(const uint64_t* keys, const uint64_t* counters, int64_t n, uint64_t* out,
+                                        void* stream) {
+  if (n < 0 || (n > 0 && (!keys || !counters || !out))) return GNA_ERR_INVALID_ARG;
+  return philox_launch(keys, counters, n, out, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_device_status(int32_t* flags, int32_t clear) {
+  if (!flags) return GNA_ERR_INVALID_ARG;
+  GNA_CUDA_TRY(cudaDeviceSynchronize());
+  int f = 0;
+  gna_status st = isgo_read_status(&f, clear);
+  if (st != GNA_OK) return st;
+  st = tc_read_status(&f, clear);
+  if (st != GNA_OK) return st;
+  *flags = f;
+  return GNA_OK;
+}

@@ -1,0 +1,26 @@
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) kernels: interface.
+#pragma once
+
+#include "common.cuh"
+
+namespace gna {
+
+enum TcOp { TC_FWD = 0, TC_ELOC = 1 };
+
+struct TcCall {
+  const gna_graph* g;
+  Dims m;
+  int op;
+  const float* theta;
+  const int8_t* spins;
+  int64_t B;
+  double* logpsi;  // TC_FWD: [B][2]
+  double* eloc;    // TC_ELOC: [B][2]
+  float* dlogpsi;  // TC_ELOC: [B][E] or NULL
+};
+
+gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes);
+gna_status tc_run(const TcCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
+gna_status tc_read_status(int* flags, int clear);
+
+}  // namespace gna

@@ -210,6 +210,32 @@ GNA_API gna_status gna_backward(const gna_graph* g, const gna_model_desc* d, con
                         const int8_t* spins, int64_t B, const double* cot, double* grad,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* Same result as gna_backward, for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment convenience of the library.
+ *
+ * Who needs it: a process whose device memory belongs to another allocator (for
+ * example a framework pool that has already reserved the free memory, so a direct
+ * cudaMalloc fails or fragments it), or a latency-critical loop that forbids
+ * allocation after start-up because cudaMalloc may synchronise the device and take an
+ * unbounded time.  This call takes no workspace and calls no cudaMalloc, cudaFree or
+ * allocating library routine: its scratch (per-block gradient partials, and per-block
+ * feature storage when a sample's features do not fit in shared memory) lives in a
+ * fixed 32 MiB array inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   Arguments and result as for gna_backward (without the workspace).
+ *   The first call on a device performs a one-time set-up (it looks up the array's
+ *   device address with that device current); make that first call before any stream
+ *   capture.
+ *   All calls share the one array, and each call overwrites what the previous one left
+ *   there (nothing in it needs to start at zero).  Calls that overlap in time on the
+ *   GPU -- on different streams or host threads -- race on it and give wrong results;
+ *   serialise them.
+ *   The block count is reduced to fit the array; a model whose single-block scratch
+ *   exceeds 32 MiB is rejected with GNA_ERR_WORKSPACE. */
+GNA_API gna_status gna_backward_static(const gna_graph* g, const gna_model_desc* d,
+                                       const void* theta, const int8_t* spins, int64_t B,
+                                       const double* cot, double* grad, void* stream);
+
 /* ISGO weights and statistics (Eq. isgo, read as the covariance gradient):
  *   log w_x = 2 (Re logpsi_x - Re logpsi0_x) + log counts_x,  p = w / sum w (float64
  *   max-shifted log-sum-exp), Ebar = sum p E, var = sum p |E - Ebar|^2,

@@ -271,6 +271,25 @@ extern "C" gna_status gna_backward(const gna_graph* g, const gna_model_desc* d, 
   return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
+extern "C" gna_status gna_backward_static(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                          const int8_t* spins, int64_t B, const double* cot, double* grad,
+                                          void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!theta || !grad || (B > 0 && (!spins || !cot))) return GNA_ERR_INVALID_ARG;
+  SimtCall sc{};
+  sc.g = g;
+  sc.m = make_dims(g, d);
+  sc.op = 4;
+  sc.theta = theta;
+  sc.spins = spins;
+  sc.B = B;
+  sc.cot = cot;
+  sc.grad = grad;
+  return simt_backward_static(sc, simt_prec(d), (cudaStream_t)stream);
+}
+
 extern "C" gna_status gna_isgo_weights_workspace(int64_t B, size_t* bytes) {
   if (!bytes || B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
   *bytes = isgo_weights_ws(B);

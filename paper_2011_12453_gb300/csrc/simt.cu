@@ -10,6 +10,7 @@
 // dense phase that writes tanh(X W + b).  The incremental local energy runs the same two
 // phases on the rows of ball_l(e) only, reading unchanged rows from the cached layers.
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -939,6 +940,101 @@ gna_status simt_launch(const SimtCall& sc, void* ws, size_t ws_bytes, cudaStream
   }
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
+}
+
+
+// ---------------------------------------------------------------------------------
+// Backward with library-owned scratch (gna_backward_static)
+// ---------------------------------------------------------------------------------
+// The per-block gradient partials -- and the per-block feature region when a sample's
+// features do not fit in shared memory -- live in this fixed array instead of a
+// caller-supplied workspace.  Every device that loads the library reserves it until
+// the process exits.  All calls on a device share it.
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_backward_scratch[kStaticScratchBytes];
+
+// Device address of the array on the current device.  Host code cannot use the
+// symbol itself (it names a host-side stand-in), so the address is looked up once per
+// device, with that device current, and cached.
+static gna_status static_scratch_address(void** out) {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  GNA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GNA_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    GNA_CUDA_TRY(cudaGetSymbolAddress(&p, g_backward_scratch));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return GNA_OK;
+}
+
+template <typename T>
+static gna_status backward_static_launch(const SimtCall& sc, cudaStream_t stream) {
+  if (sc.B == 0) {
+    GNA_CUDA_TRY(cudaMemsetAsync(sc.grad, 0, sc.m.P * sizeof(double), stream));
+    return GNA_OK;
+  }
+  Plan p;
+  gna_status st = simt_plan<T>(sc.g, sc.m, OP_BWD, sc.B, &p);
+  if (st != GNA_OK) return st;
+  // Fit the grid to the array: each block needs its partial (and its region when the
+  // region is not in shared memory).  A single block that does not fit is an error.
+  const size_t region_bytes = p.region_in_smem ? 0 : p.region_elems * sizeof(T);
+  const size_t per_block = region_bytes + (size_t)sc.m.P * sizeof(double);
+  const size_t usable = kStaticScratchBytes - 512;  // two 256-byte alignment pads
+  int64_t grid = (int64_t)(usable / per_block);
+  if (grid < 1) return GNA_ERR_WORKSPACE;
+  if (grid > p.grid) grid = p.grid;
+  void* base = nullptr;
+  st = static_scratch_address(&base);
+  if (st != GNA_OK) return st;
+  SimtArgs<T> a;
+  a.g = sc.g->d;
+  a.m = sc.m;
+  a.op = OP_BWD;
+  a.G = p.G;
+  for (int l = 0; l <= kMaxL; ++l) a.maxball[l] = (l <= sc.m.L && l <= sc.g->d.Lmax) ? sc.g->max_ball[l] : 0;
+  a.theta = (const T*)sc.theta;
+  a.spins = sc.spins;
+  a.B = sc.B;
+  a.logpsi = nullptr;
+  a.eloc = nullptr;
+  a.dlogpsi = nullptr;
+  a.cot = sc.cot;
+  a.chain_spins = nullptr;
+  a.n_sweeps = 0;
+  a.record_every = 0;
+  a.seed = 0;
+  a.step0 = 0;
+  a.samples_out = nullptr;
+  a.logpsi_out = nullptr;
+  a.n_acc = nullptr;
+  a.trace = nullptr;
+  a.region_elems = p.region_elems;
+  a.region_in_smem = p.region_in_smem;
+  a.partial_in_smem = p.partial_in_smem;
+  // Every block zeroes its own partial before accumulating and the reduction reads
+  // only what this launch wrote, so nothing left by an earlier call is used.
+  unsigned char* w = (unsigned char*)base;
+  a.gregion = nullptr;
+  if (!p.region_in_smem) {
+    a.gregion = (T*)w;
+    w += align_up((size_t)grid * region_bytes);
+  }
+  a.partial = (double*)w;
+  k_backward<T><<<(int)grid, kThreads, p.smem, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  k_reduce_partials<<<(sc.m.P + 255) / 256, 256, 0, stream>>>(a.partial, (int)grid, sc.m.P, sc.grad);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+gna_status simt_backward_static(const SimtCall& sc, int prec, cudaStream_t stream) {
+  return prec == GNA_PREC_FP64 ? backward_static_launch<double>(sc, stream) : backward_static_launch<float>(sc, stream);
 }
 
 gna_status simt_workspace(const gna_graph* g, const Dims& m, int prec, int op, int64_t B, size_t* bytes) {

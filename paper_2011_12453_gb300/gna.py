@@ -32,7 +32,7 @@ OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIG
 EXPORTED = [
     "gna_version", "gna_status_string", "gna_graph_create", "gna_graph_destroy", "gna_graph_info",
     "gna_ball_sizes_host", "gna_model_desc_init", "gna_num_params", "gna_workspace_size", "gna_forward",
-    "gna_local_energy", "gna_metropolis_sweep", "gna_backward", "gna_isgo_weights_workspace",
+    "gna_local_energy", "gna_metropolis_sweep", "gna_backward", "gna_backward_static", "gna_isgo_weights_workspace",
     "gna_isgo_weights", "isgo_grad",
     "gna_sgd_update", "gna_philox4x64_10", "gna_device_status",
 ]
@@ -84,6 +84,7 @@ def lib():
             "gna_metropolis_sweep": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, i32, i32, u64, u64,
                                            vp, vp, vp, vp, vp, sz, vp]),
             "gna_backward": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]),
+            "gna_backward_static": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, vp]),
             "gna_isgo_weights_workspace": (i32, [i64, ctypes.POINTER(sz)]),
             "gna_isgo_weights": (i32, [vp, vp, vp, vp, i64, vp, vp, vp, sz, vp]),
             "isgo_grad": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, vp, vp, i64, vp, vp, vp, sz, vp]),
@@ -294,6 +295,19 @@ def backward(graph: Graph, model: Model, theta, spins, cot, out=None):
     w, wn = _ws_for(graph, model, OP_BACKWARD, B)
     _check(lib().gna_backward(graph.handle, ctypes.byref(model.desc), theta.data_ptr(), spins.data_ptr(), B,
                               cot.data_ptr(), g.data_ptr(), w, wn, _stream()), "gna_backward")
+    return g
+
+
+def backward_static(graph: Graph, model: Model, theta, spins, cot, out=None):
+    """As backward(), through gna_backward_static: no workspace, no device allocation by
+    the library (its scratch is a fixed array inside libgna.so shared by all calls)."""
+    torch = _check_theta(model, theta)
+    _check_spins(graph, spins)
+    B = spins.shape[0]
+    g = out if out is not None else torch.empty(model.num_params, dtype=torch.float64, device=theta.device)
+    cot = cot.contiguous()
+    _check(lib().gna_backward_static(graph.handle, ctypes.byref(model.desc), theta.data_ptr(), spins.data_ptr(), B,
+                                     cot.data_ptr(), g.data_ptr(), _stream()), "gna_backward_static")
     return g
 
 

@@ -1,10 +1,776 @@
-// Tensor-core BF16 kernels (placeholder until the tcgen05 path lands).
+// Tensor-core path: BF16 node-feature GEMMs on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), for the GCN forward and the incremental
+// local energy of arXiv:2011.12453 (Eq. gcn; local energy of the scaling section).
+//
+// One CTA owns one configuration at a time (persistent grid).  Per GCN layer, the rows
+// to recompute are gathered into BF16 A tiles of 128 rows x 2F in shared memory, laid
+// out in the no-swizzle K-major canonical form the MMA reads: element (r, k) of a tile at
+// (r/8)*SBO + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes, SBO = 32F.  B = W^T (F x 2F) uses the
+// same form.  One elected thread issues 2F/16 MMAs of M=128, N=F, K=16 per tile into a
+// TMEM accumulator (column offset tile*F) and commits them to an mbarrier; all warps
+// then read the accumulator with tcgen05.ld (warp w sees lanes 32*(w%4)..+31, warp
+// group w/4 takes half of the columns), add the bias, apply tanh and store the new rows.
+//
+// Storage: layers 0..L-1 (cached and recomputed) are BF16, as the GEMM consumes them;
+// layer L is FP32, so that Delta log Psi = w_r . sum (h_new - h_old) over the last
+// layer keeps FP32 differences.  Incremental bond groups stack the rows of several
+// antiparallel bonds at the same layer into the same tiles.
+//
+// Every wait on the mbarrier is bounded: on timeout the kernel records bit 1 in its
+// status word, waits (bounded again) for the MMAs in flight, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <climits>
+#include <cstring>
+
 #include "tc.cuh"
 
 namespace gna {
 
-gna_status tc_workspace(const gna_graph*, const Dims&, int, int64_t, size_t*) { return GNA_ERR_UNSUPPORTED; }
-gna_status tc_run(const TcCall&, void*, size_t, cudaStream_t) { return GNA_ERR_UNSUPPORTED; }
-gna_status tc_read_status(int*, int) { return GNA_OK; }
+static __device__ int s_tc_status;
+
+constexpr int kTcThreads = 256;
+constexpr int kTmemCols = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;            // try_wait iterations
+constexpr uint64_t kWaitNs = 2000000000ull;          // and at most 2 s of wall time
+
+// ---------------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation, M = 128, N = F.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 8 columns of FP32 from TMEM; thread i of the warp gets lane (base + i).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+  v[4] = __uint_as_float(r4);
+  v[5] = __uint_as_float(r5);
+  v[6] = __uint_as_float(r6);
+  v[7] = __uint_as_float(r7);
+}
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------
+// layout (computed on the host, passed in the arguments)
+// ---------------------------------------------------------------------------------
+struct TcLayout {
+  // shared memory byte offsets
+  uint32_t oWt, obias, oemb, owr, obr, oA, ospin, oint, odbl, obar, oslot, oregion, smem_total;
+  // region (shared or global) byte offsets
+  uint64_t rcache16, rcacheL, rnew16, rnewL, region_bytes;
+  uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's rows (bytes from rnew16)
+  int T;                          // A tiles (TMEM holds T accumulators of F columns)
+  int G;                          // bonds per group
+};
+
+struct TcArgs {
+  DevGraph g;
+  Dims m;
+  int op;
+  TcLayout lay;
+  int maxball[kMaxL + 1];
+  const float* theta;
+  const int8_t* spins;
+  int64_t B;
+  double* logpsi;
+  double* eloc;
+  float* dlogpsi;
+  unsigned char* gregion;  // [grid][region_bytes] when the region is not in shared memory
+  int region_in_smem;
+};
+
+__host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int region_in_smem, TcLayout* t) {
+  const int F = m.F, N = m.N, L = m.L;
+  uint64_t o = 0;
+  auto take = [&](uint64_t bytes, uint64_t align) {
+    o = (o + align - 1) / align * align;
+    uint64_t r = o;
+    o += bytes;
+    return (uint32_t)r;
+  };
+  t->T = kTmemCols / F;
+  t->G = G;
+  t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
+  t->oA = take((uint64_t)t->T * 128 * 2 * F * 2, 1024);
+  t->obias = take(F * 4, 16);
+  t->oemb = take(2 * F * 4, 16);
+  t->owr = take((F + 2) * 2 * 4, 16);
+  t->obr = take(16, 16);
+  t->ospin = take(N, 16);
+  t->oint = take(((uint64_t)m.E + G + (L + 1) * (G + 1) + 16) * 4, 16);
+  t->odbl = take((uint64_t)(2 * G + 16 + kTcThreads) * 8, 16);
+  t->obar = take(8, 8);
+  t->oslot = take(4, 4);
+  // region
+  uint64_t r = 0;
+  auto rtake = [&](uint64_t bytes) {
+    r = (r + 15) / 16 * 16;
+    uint64_t x = r;
+    r += bytes;
+    return x;
+  };
+  t->rcache16 = rtake((uint64_t)L * N * F * 2);
+  t->rcacheL = rtake((uint64_t)N * F * 4);
+  uint64_t n16 = 0;
+  for (int l = 0; l < L; ++l) {
+    t->new16_off[l] = n16;
+    n16 += (uint64_t)G * maxball[l] * F * 2;
+  }
+  t->rnew16 = rtake(n16);
+  t->rnewL = rtake((uint64_t)G * maxball[L] * F * 4);
+  t->region_bytes = (r + 255) / 256 * 256;
+  if (region_in_smem) {
+    t->oregion = take(t->region_bytes, 16);
+  } else {
+    t->oregion = 0;
+  }
+  t->smem_total = (uint32_t)o;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// device pieces
+// ---------------------------------------------------------------------------------
+struct TcCtx {
+  const TcArgs* a;
+  int N, F, L, E, T, G;
+  unsigned char* smem;
+  __nv_bfloat16* Wt;
+  unsigned char* A;
+  float *bias, *emb, *wr, *br;
+  int8_t* spin;
+  int* sint;
+  double* sdbl;
+  uint64_t* bar;
+  uint32_t* slot;
+  unsigned char* region;
+  uint32_t tbase;
+  uint32_t phase;
+  int* fail;  // shared flag
+};
+
+__device__ __forceinline__ unsigned char* a_row_chunk(const TcCtx& c, int q, int chunk) {
+  // 16-byte chunk `chunk` (k = 8*chunk .. 8*chunk+7) of row q of the stacked A tiles
+  const int tile = q >> 7, qq = q & 127;
+  return c.A + (size_t)tile * 128 * 4 * c.F + (size_t)(qq >> 3) * (32 * c.F) + chunk * 128 + (qq & 7) * 16;
+}
+
+__device__ __forceinline__ const __nv_bfloat16* cache16(const TcCtx& c, int l) {
+  return (const __nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.F;
+}
+__device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
+  return (__nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.F;
+}
+__device__ __forceinline__ float* cacheL(const TcCtx& c) { return (float*)(c.region + c.a->lay.rcacheL); }
+__device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, int l) {
+  return (__nv_bfloat16*)(c.region + c.a->lay.rnew16 + c.a->lay.new16_off[l]);
+}
+__device__ __forceinline__ float* newL(const TcCtx& c) { return (float*)(c.region + c.a->lay.rnewL); }
+
+// acc[0..8) += w * bf16 row chunk at p (16 bytes)
+__device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat16* p) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  acc[0] += w * bf16lo(u.x);
+  acc[1] += w * bf16hi(u.x);
+  acc[2] += w * bf16lo(u.y);
+  acc[3] += w * bf16hi(u.y);
+  acc[4] += w * bf16lo(u.z);
+  acc[5] += w * bf16hi(u.z);
+  acc[6] += w * bf16lo(u.w);
+  acc[7] += w * bf16hi(u.w);
+}
+
+// Issue the MMAs of nt tiles (thread 0), commit, and wait (bounded).  Returns false on
+// timeout (uniform across the CTA).
+__device__ bool run_mmas(TcCtx& c, int nt) {
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    const int F = c.F;
+    const uint32_t idesc = idesc_bf16(128, F);
+    const uint32_t sbo = 32 * F;
+    const uint32_t a0 = smem_u32(c.A), b0 = smem_u32(c.Wt);
+    for (int t = 0; t < nt; ++t) {
+      for (int kb = 0; kb < (2 * F) / 16; ++kb) {
+        const uint64_t ad = sdesc(a0 + t * 128 * 4 * F + kb * 256, 128, sbo);
+        const uint64_t bd = sdesc(b0 + kb * 256, 128, sbo);
+        mma_bf16(c.tbase + t * F, ad, bd, idesc, kb > 0 ? 1u : 0u);
+      }
+    }
+    mma_commit(c.bar);
+    const bool ok = mbar_wait_bounded(c.bar, c.phase);
+    if (!ok) {
+      *c.fail = 1;
+      atomicOr(&s_tc_status, 1);
+    }
+  }
+  c.phase ^= 1u;
+  __syncthreads();
+  tc_fence_after();
+  return *c.fail == 0;
+}
+
+// Epilogue: rows [0, R) of the nt accumulators -> tanh(acc + b) stored to out (BF16 rows
+// of F, or FP32 rows when out_f32).
+__device__ void epilogue(const TcCtx& c, int nt, int R, void* out, bool out_f32) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q4 = warp & 3, wg = warp >> 2;
+  const int F = c.F, half = F / 2;
+  for (int t = 0; t < nt; ++t) {
+    const int q = t * 128 + q4 * 32 + lane;
+    for (int j = 0; j < half / 8; ++j) {
+      const int col = wg * half + j * 8;
+      float v[8];
+      tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), v);
+      if (q < R) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = tanh_fast(v[i] + c.bias[col + i]);
+        if (out_f32) {
+          float4* o = reinterpret_cast<float4*>((float*)out + (size_t)q * F + col);
+          o[0] = make_float4(v[0], v[1], v[2], v[3]);
+          o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+          uint4 w;
+          w.x = pack_bf16(v[0], v[1]);
+          w.y = pack_bf16(v[2], v[3]);
+          w.z = pack_bf16(v[4], v[5]);
+          w.w = pack_bf16(v[6], v[7]);
+          *reinterpret_cast<uint4*>((__nv_bfloat16*)out + (size_t)q * F + col) = w;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
+// Forward of the configuration in c.spin: fills the cache (layers 0..L-1 BF16, L FP32).
+__device__ bool tc_forward(TcCtx& c) {
+  const int N = c.N, F = c.F, L = c.L;
+  const DevGraph& g = c.a->g;
+  // layer 0: embedding rows
+  __nv_bfloat16* c0 = cache16w(c, 0);
+  for (int i = threadIdx.x; i < N * F; i += blockDim.x)
+    c0[i] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
+  __syncthreads();
+  const int C8 = (2 * F) / 8, F8 = F / 8;
+  const int rows_per_pass = c.T * 128;
+  for (int l = 1; l <= L; ++l) {
+    const __nv_bfloat16* hp = cache16(c, l - 1);
+    for (int r0 = 0; r0 < N; r0 += rows_per_pass) {
+      const int R = min(rows_per_pass, N - r0);
+      const int nt = (R + 127) / 128;
+      const int items = ((R + 7) / 8) * 8 * C8;
+      for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int q8 = idx & 7, ch = (idx >> 3) % C8, qb = (idx >> 3) / C8;
+        const int q = qb * 8 + q8;
+        if (q >= R) continue;
+        const int v = r0 + q;
+        uint4 outw;
+        if (ch < F8) {
+          float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          const int k1 = __ldg(g.row_ptr + v + 1);
+          for (int k = __ldg(g.row_ptr + v); k < k1; ++k)
+            fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * F + ch * 8);
+          outw.x = pack_bf16(acc[0], acc[1]);
+          outw.y = pack_bf16(acc[2], acc[3]);
+          outw.z = pack_bf16(acc[4], acc[5]);
+          outw.w = pack_bf16(acc[6], acc[7]);
+        } else {
+          outw = *reinterpret_cast<const uint4*>(hp + (size_t)v * F + (ch - F8) * 8);
+        }
+        *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
+      }
+      if (!run_mmas(c, nt)) return false;
+      if (l < L)
+        epilogue(c, nt, R, cache16w(c, l) + (size_t)r0 * F, false);
+      else
+        epilogue(c, nt, R, cacheL(c) + (size_t)r0 * F, true);
+    }
+  }
+  return true;
+}
+
+// log Psi readout from the FP32 last layer (valid in thread 0), deterministic order.
+__device__ void tc_readout(const TcCtx& c, double out[2]) {
+  const int N = c.N, F = c.F;
+  float* red = (float*)(c.sdbl + 2 * c.G + 16);
+  const float* HL = cacheL(c);
+  const int parts = blockDim.x / F;
+  const int f = threadIdx.x % F, part = threadIdx.x / F;
+  if (part < parts) {
+    float acc = 0.f;
+    for (int v = part; v < N; v += parts) acc += HL[(size_t)v * F + f];
+    red[part * F + f] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float re = 0.f, im = 0.f;
+    for (int ff = threadIdx.x; ff < F; ff += 32) {
+      float z = 0.f;
+      for (int p = 0; p < parts; ++p) z += red[p * F + ff];
+      re += z * c.wr[2 * ff];
+      im += z * c.wr[2 * ff + 1];
+    }
+    re = warp_sum_t(re);
+    im = warp_sum_t(im);
+    if (threadIdx.x == 0) {
+      int up = 0;
+      for (int v = 0; v < N; ++v) up += c.spin[v] > 0;
+      const int dn = N - up;
+      out[0] = (double)(re + (float)up * c.wr[2 * F] + (float)dn * c.wr[2 * (F + 1)] + c.br[0]);
+      out[1] = (double)(im + (float)up * c.wr[2 * F + 1] + (float)dn * c.wr[2 * (F + 1) + 1] + c.br[1]);
+    }
+  }
+  __syncthreads();
+}
+
+// Rows of a bond group at layer l: gather into the A tiles.
+__device__ void gather_group(const TcCtx& c, int l, const int* slot_e, int nb, const int* soff) {
+  const DevGraph& g = c.a->g;
+  const int F = c.F, G = c.G, Lm = g.Lmax;
+  (void)Lm;
+  const int C8 = (2 * F) / 8, F8 = F / 8;
+  const int* offp = soff + (l - 1) * (G + 1);
+  const int* offl = soff + l * (G + 1);
+  const int R = offl[nb];
+  const __nv_bfloat16* cp = cache16(c, l - 1);
+  const __nv_bfloat16* np = new16(c, l - 1);
+  const int items = ((R + 7) / 8) * 8 * C8;
+  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+    const int q8 = idx & 7, ch = (idx >> 3) % C8, qb = (idx >> 3) / C8;
+    const int q = qb * 8 + q8;
+    if (q >= R) continue;
+    int k = 0;
+    while (k + 1 < nb && offl[k + 1] <= q) ++k;
+    const int r = q - offl[k];
+    const int e = slot_e[k];
+    const int bo = __ldg(g.ball_off + e);
+    const int sprev = offp[k + 1] - offp[k];
+    const __nv_bfloat16* nrow = np + (size_t)offp[k] * F;
+    const int v = __ldg(g.ball_vert + bo + r);
+    uint4 outw;
+    if (ch < F8) {
+      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const int nb0 = __ldg(g.row_nbr + bo + r);
+      const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+      for (int kk = k0; kk < k1; ++kk) {
+        const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
+        const __nv_bfloat16* src = p < sprev ? nrow + (size_t)p * F : cp + (size_t)__ldg(g.col + kk) * F;
+        fma_chunk(acc, __ldg(g.wf + kk), src + ch * 8);
+      }
+      outw.x = pack_bf16(acc[0], acc[1]);
+      outw.y = pack_bf16(acc[2], acc[3]);
+      outw.z = pack_bf16(acc[4], acc[5]);
+      outw.w = pack_bf16(acc[6], acc[7]);
+    } else {
+      const __nv_bfloat16* src = r < sprev ? nrow + (size_t)r * F : cp + (size_t)v * F;
+      outw = *reinterpret_cast<const uint4*>(src + (ch - F8) * 8);
+    }
+    *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
+  }
+}
+
+// Incremental Delta log Psi of the bonds slot_e[0..nb): results in sdbl[2k], sdbl[2k+1].
+__device__ bool tc_group(TcCtx& c, const int* slot_e, int nb, int* soff) {
+  const DevGraph& g = c.a->g;
+  const int F = c.F, L = c.L, G = c.G, Lm = g.Lmax;
+  if (threadIdx.x == 0) {
+    for (int l = 0; l <= L; ++l) {
+      int o = 0;
+      for (int k = 0; k < nb; ++k) {
+        soff[l * (G + 1) + k] = o;
+        o += __ldg(g.ball_size + (size_t)slot_e[k] * (Lm + 1) + l);
+      }
+      soff[l * (G + 1) + nb] = o;
+    }
+  }
+  __syncthreads();
+  // layer 0: the exchanged pair takes each other's embedding rows
+  __nv_bfloat16* n0 = new16(c, 0);
+  for (int i = threadIdx.x; i < nb * 2 * F; i += blockDim.x) {
+    const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
+    const int e = slot_e[k];
+    const int other = __ldg(g.edges + 2 * e + (1 - r));
+    n0[(size_t)(soff[k] + r) * F + f] = __float2bfloat16_rn(c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f]);
+  }
+  __syncthreads();
+  for (int l = 1; l <= L; ++l) {
+    gather_group(c, l, slot_e, nb, soff);
+    const int R = soff[l * (G + 1) + nb];
+    const int nt = (R + 127) / 128;
+    if (!run_mmas(c, nt)) return false;
+    if (l < L)
+      epilogue(c, nt, R, new16(c, l), false);
+    else
+      epilogue(c, nt, R, newL(c), true);
+  }
+  // Delta_k = sum_{r in ball_L} (new - old) . w_r[:, k]   (one warp per bond)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const float* cL = cacheL(c);
+  const float* nL = newL(c);
+  const int* offL = soff + L * (G + 1);
+  for (int k = warp; k < nb; k += nwarps) {
+    const int e = slot_e[k];
+    const int bo = __ldg(g.ball_off + e);
+    const int R = offL[k + 1] - offL[k];
+    const float* nrow = nL + (size_t)offL[k] * F;
+    float dre = 0.f, dim = 0.f;
+    for (int i = lane; i < R * F; i += 32) {
+      const int r = i / F, f = i % F;
+      const int v = __ldg(g.ball_vert + bo + r);
+      const float d = nrow[i] - cL[(size_t)v * F + f];
+      dre += d * c.wr[2 * f];
+      dim += d * c.wr[2 * f + 1];
+    }
+    dre = warp_sum_t(dre);
+    dim = warp_sum_t(dim);
+    if (lane == 0) {
+      c.sdbl[2 * k] = (double)dre;
+      c.sdbl[2 * k + 1] = (double)dim;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_fail;
+  __shared__ int s_count;
+  TcCtx c;
+  c.a = &a;
+  c.N = a.m.N;
+  c.F = a.m.F;
+  c.L = a.m.L;
+  c.E = a.m.E;
+  c.T = a.lay.T;
+  c.G = a.lay.G;
+  c.smem = smem;
+  c.Wt = (__nv_bfloat16*)(smem + a.lay.oWt);
+  c.A = smem + a.lay.oA;
+  c.bias = (float*)(smem + a.lay.obias);
+  c.emb = (float*)(smem + a.lay.oemb);
+  c.wr = (float*)(smem + a.lay.owr);
+  c.br = (float*)(smem + a.lay.obr);
+  c.spin = (int8_t*)(smem + a.lay.ospin);
+  c.sint = (int*)(smem + a.lay.oint);
+  c.sdbl = (double*)(smem + a.lay.odbl);
+  c.bar = (uint64_t*)(smem + a.lay.obar);
+  c.slot = (uint32_t*)(smem + a.lay.oslot);
+  c.region = a.region_in_smem ? smem + a.lay.oregion : a.gregion + (size_t)blockIdx.x * a.lay.region_bytes;
+  c.fail = &s_fail;
+  c.phase = 0;
+  const int F = c.F, N = c.N;
+  const Dims& m = a.m;
+  const float* th = a.theta;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(c.bar, 1);
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    tmem_alloc(c.slot, kTmemCols);
+    tmem_relinquish();
+  }
+  // W^T (n = output feature, k = input feature) in the canonical K-major layout
+  const float* W = th + m.oW;
+  for (int i = threadIdx.x; i < F * 2 * F; i += blockDim.x) {
+    const int n = i / (2 * F), k = i % (2 * F);
+    unsigned char* p = (unsigned char*)c.Wt + (size_t)(n >> 3) * (32 * F) + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+  }
+  for (int i = threadIdx.x; i < F; i += blockDim.x) c.bias[i] = th[m.ob + i];
+  for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
+  for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) c.wr[i] = th[m.owr + i];
+  if (threadIdx.x < 2) c.br[threadIdx.x] = th[m.obr + threadIdx.x];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  c.tbase = *c.slot;
+
+  int* list = c.sint;
+  int* slot_e = c.sint + c.E;
+  int* soff = slot_e + c.G;
+  bool ok = true;
+  for (int64_t b = blockIdx.x; b < a.B && ok; b += gridDim.x) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) c.spin[i] = a.spins[b * N + i];
+    __syncthreads();
+    ok = tc_forward(c);
+    if (!ok) break;
+    if (a.op == TC_FWD) {
+      double lp[2];
+      tc_readout(c, lp);
+      if (threadIdx.x == 0) {
+        a.logpsi[2 * b] = lp[0];
+        a.logpsi[2 * b + 1] = lp[1];
+      }
+      continue;
+    }
+    // antiparallel bonds (ordered) and the diagonal energy
+    double diag = 0.0;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      int count = 0;
+      double d = 0.0;
+      for (int base = 0; base < c.E; base += 32) {
+        const int e = base + lane;
+        bool anti = false;
+        if (e < c.E) {
+          const int i = __ldg(a.g.edges + 2 * e), j = __ldg(a.g.edges + 2 * e + 1);
+          const int si = c.spin[i], sj = c.spin[j];
+          anti = si != sj;
+          d += __ldg(a.g.J + e) * 0.25 * (double)(si * sj);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, anti);
+        if (anti) list[count + __popc(mask & ((1u << lane) - 1u))] = e;
+        count += __popc(mask);
+      }
+      d = warp_sum_t(d);
+      if (lane == 0) {
+        s_count = count;
+        diag = d;
+      }
+    }
+    if (a.dlogpsi)
+      for (int e = threadIdx.x; e < c.E; e += blockDim.x) a.dlogpsi[b * c.E + e] = 0.f;
+    __syncthreads();
+    const int na = s_count;
+    double er = diag, ei = 0.0;
+    for (int t0 = 0; t0 < na && ok; t0 += c.G) {
+      const int nb = min(c.G, na - t0);
+      if (threadIdx.x < nb) slot_e[threadIdx.x] = list[t0 + threadIdx.x];
+      __syncthreads();
+      ok = tc_group(c, slot_e, nb, soff);
+      if (!ok) break;
+      if (threadIdx.x == 0) {
+        for (int k = 0; k < nb; ++k) {
+          const int e = slot_e[k];
+          const float dre = (float)c.sdbl[2 * k], dim = (float)c.sdbl[2 * k + 1];
+          const float amp = expf(dre);
+          float sn, cs;
+          sincosf(dim, &sn, &cs);
+          const double J = __ldg(a.g.J + e);
+          er += 0.5 * J * (double)(amp * cs);
+          ei += 0.5 * J * (double)(amp * sn);
+          if (a.dlogpsi) a.dlogpsi[b * c.E + e] = dre;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && ok) {
+      a.eloc[2 * b] = er;
+      a.eloc[2 * b + 1] = ei;
+    }
+    __syncthreads();
+  }
+  // teardown: on failure wait (bounded) for the MMAs in flight before freeing TMEM
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(c.bar, c.phase ^ 1u);  // the phase that timed out
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(c.tbase, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------------
+struct TcPlan {
+  TcLayout lay;
+  int grid = 0;
+  int region_in_smem = 0;
+  size_t ws_bytes = 0;
+};
+
+static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, TcPlan* p, int* maxball) {
+  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared) return GNA_ERR_UNSUPPORTED;
+  DeviceInfo di;
+  gna_status st = device_info(&di);
+  if (st != GNA_OK) return st;
+  if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
+  for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
+  const int T = kTmemCols / m.F;
+  const size_t budget = (size_t)di.smem_optin - 1024;
+  int G = op == TC_ELOC ? (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1) : 1;
+  if (G > 16) G = 16;
+  if (G < 1) return GNA_ERR_UNSUPPORTED;  // one bond's last-layer rows exceed the TMEM tiles
+  TcLayout lay;
+  // prefer the whole region in shared memory with as many bonds per group as fit
+  int g_fit = 0;
+  for (int gg = G; gg >= 1; --gg) {
+    tc_layout(m, maxball, gg, 1, &lay);
+    if (lay.smem_total <= budget) {
+      g_fit = gg;
+      break;
+    }
+  }
+  if (g_fit > 0) {
+    p->region_in_smem = 1;
+  } else {
+    tc_layout(m, maxball, G, 0, &lay);
+    if (lay.smem_total > budget) return GNA_ERR_UNSUPPORTED;
+    p->region_in_smem = 0;
+  }
+  // At most 512 / kTmemCols CTAs may hold TMEM on one SM at a time: request enough shared
+  // memory that no more than that many are resident.
+  const uint32_t min_smem = (uint32_t)(228u * 1024u / (512 / kTmemCols + 1)) + 1024u;
+  if (lay.smem_total < min_smem) lay.smem_total = min_smem;
+  p->lay = lay;
+  GNA_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_total));
+  int occ = 0;
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_tc, kTcThreads, lay.smem_total));
+  if (occ < 1) occ = 1;
+  if (occ * kTmemCols > 512) return GNA_ERR_UNSUPPORTED;
+  int64_t grid = (int64_t)di.sms * occ;
+  if (grid > B) grid = B;
+  if (grid < 1) grid = 1;
+  p->grid = (int)grid;
+  p->ws_bytes = p->region_in_smem ? 0 : align_up((size_t)grid * lay.region_bytes);
+  return GNA_OK;
+}
+
+gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes) {
+  if (B == 0) {
+    *bytes = 0;
+    return GNA_OK;
+  }
+  TcPlan p;
+  int maxball[kMaxL + 1];
+  gna_status st = tc_plan(g, m, op, B, &p, maxball);
+  if (st != GNA_OK) return st;
+  *bytes = p.ws_bytes;
+  return GNA_OK;
+}
+
+gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (call.B == 0) return GNA_OK;
+  TcPlan p;
+  TcArgs a;
+  gna_status st = tc_plan(call.g, call.m, call.op, call.B, &p, a.maxball);
+  if (st != GNA_OK) return st;
+  if (ws_bytes < p.ws_bytes || (p.ws_bytes > 0 && !ws)) return GNA_ERR_WORKSPACE;
+  a.g = call.g->d;
+  a.m = call.m;
+  a.op = call.op;
+  a.lay = p.lay;
+  a.theta = call.theta;
+  a.spins = call.spins;
+  a.B = call.B;
+  a.logpsi = call.logpsi;
+  a.eloc = call.eloc;
+  a.dlogpsi = call.dlogpsi;
+  a.gregion = (unsigned char*)ws;
+  a.region_in_smem = p.region_in_smem;
+  k_tc<<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+gna_status tc_read_status(int* flags, int clear) {
+  int v = 0;
+  GNA_CUDA_TRY(cudaMemcpyFromSymbol(&v, s_tc_status, sizeof(int)));
+  *flags |= v;
+  if (clear) {
+    int z = 0;
+    GNA_CUDA_TRY(cudaMemcpyToSymbol(s_tc_status, &z, sizeof(int)));
+  }
+  return GNA_OK;
+}
 
 }  // namespace gna

@@ -1,0 +1,116 @@
+"""GPU parity of the BF16 tensor-core path (tcgen05 GEMMs, FP32 accumulation) against the
+FP64 oracle run on the same parameters with the GEMM weights W rounded to BF16, so the
+stated error is that of the activations' rounding.
+
+Tolerances: 2e-2 relative on log Psi; local energy per sample within 2e-3 relative and
+the batch mean within 1e-4 relative of the FP32 full re-evaluation."""
+import numpy as np
+import pytest
+
+from oracle import gcn, heisenberg as hz
+from paper_2011_12453_gb300 import build as B, gna, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    B.build()
+    t.cuda.set_device(0)
+    return t
+
+
+def _round_W_bf16(torch, th, F, L):
+    """theta with the GCN weight matrix W rounded to BF16 (the GEMM operand)."""
+    out = th.copy()
+    o = 3 * F
+    w = torch.tensor(out[o:o + 2 * F * F], dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    out[o:o + 2 * F * F] = w
+    return out
+
+
+def _setup(torch, g, F, L, seed=0, scale=0.1):
+    th = W.random_theta(F, L, seed=seed, scale=scale)
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_BF16)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda")
+    th_or = _round_W_bf16(torch, theta.double().cpu().numpy(), F, L)
+    Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
+    return graph, model, theta, th_or, Ah
+
+
+CASES = [("kagome2", 16, 2), ("kagome6", 32, 4), ("tri12", 48, 4), ("tri6", 64, 3), ("er40", 32, 3)]
+
+
+def _graph(name):
+    return {"kagome2": W.kagome(2), "kagome6": W.kagome(6), "tri12": W.triangular(12, 12), "tri6": W.triangular(6, 6),
+            "er40": W.erdos_renyi(40, 0.1, seed=3, J_range=(0.5, 1.5))}[name]
+
+
+@pytest.mark.parametrize("name,F,L", CASES)
+def test_bf16_forward_parity(torch, name, F, L):
+    g = _graph(name)
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.3)
+    for Bn in (33, 1):
+        s = W.random_spins(g.n_sites, Bn, seed=7 + Bn)
+        got = gna.forward(graph, model, theta, torch.tensor(s, device="cuda")).cpu().numpy()
+        want = gcn.logpsi(th, F, L, Ah, s)
+        err = np.abs(got - want).max()
+        assert err <= 2e-2 * max(1.0, np.abs(want).max()), err
+
+
+@pytest.mark.parametrize("name,F,L", CASES)
+def test_bf16_local_energy_parity(torch, name, F, L):
+    g = _graph(name)
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.3)
+    s = W.random_spins(g.n_sites, 6, seed=11)
+    E, dl = gna.local_energy(graph, model, theta, torch.tensor(s, device="cuda"), gna.ELOC_INCREMENTAL, bonds=True)
+    E = E.cpu().numpy()
+    Ec = E[:, 0] + 1j * E[:, 1]
+    want = hz.local_energy(lambda x: gcn.logpsi_complex(th, F, L, Ah, x), g.edges, g.J, s)
+    rel = np.abs(Ec - want) / np.abs(want).clip(1.0)
+    assert rel.max() <= 2e-3, rel.max()
+    d = hz.bond_log_ratios(lambda x: gcn.logpsi_complex(th, F, L, Ah, x), g.edges, s)
+    want_d = np.where(np.isnan(d.real), 0.0, d.real)
+    assert np.abs(dl.cpu().numpy() - want_d).max() <= 5e-3
+
+
+def test_bf16_incremental_mean_energy_matches_fp32_full(torch):
+    # Kagome 6x6x3, L = 4, F = 32: batch-mean energy agreement <= 1e-4 relative
+    g = W.kagome(6)
+    F, L = 32, 4
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.1)
+    m32 = gna.Model(F, L, gna.PREC_FP32)
+    s = torch.tensor(W.random_spins(g.n_sites, 4096, seed=2), device="cuda")
+    Eb = gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL).cpu().numpy()
+    Ef = gna.local_energy(graph, m32, theta, s, gna.ELOC_FULL).cpu().numpy()
+    assert abs(Eb[:, 0].mean() - Ef[:, 0].mean()) <= 1e-4 * abs(Ef[:, 0].mean())
+    assert np.max(np.abs(Eb[:, 0] - Ef[:, 0]) / np.abs(Ef[:, 0])) <= 2e-3
+
+
+def test_bf16_two_site_is_quarter(torch):
+    g = W.two_site()
+    graph, model, theta, th, Ah = _setup(torch, g, 16, 2, scale=1.0)
+    E = gna.local_energy(graph, model, theta, torch.tensor([[1, -1], [-1, 1]], dtype=torch.int8, device="cuda"),
+                         gna.ELOC_INCREMENTAL).cpu().numpy()
+    # the two exchanged rows have identical inputs after the swap: Delta = 0 exactly
+    assert np.abs(E[:, 0] - 0.25).max() < 1e-6
+
+
+def test_bf16_unshared_is_unsupported(torch):
+    g = W.kagome(2)
+    graph = gna.Graph.from_workload(g, 2)
+    model = gna.Model(16, 2, gna.PREC_BF16, shared=False)
+    with pytest.raises(gna.GnaError) as ei:
+        gna.workspace_size(graph, model, gna.OP_ELOC_INCR, 4)
+    assert ei.value.status == gna.GNA_ERR_UNSUPPORTED
+
+
+def test_bf16_device_status_clean(torch):
+    g = W.kagome(6)
+    graph, model, theta, th, Ah = _setup(torch, g, 32, 4)
+    s = torch.tensor(W.random_spins(g.n_sites, 300, seed=5), device="cuda")
+    gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL)
+    assert gna.device_status(clear=True) == 0

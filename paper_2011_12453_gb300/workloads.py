@@ -183,3 +183,22 @@ def all_sector_states(n_sites: int, n_up: int | None = None) -> np.ndarray:
         for v in range(n_sites):
             out[k, v] = 1 if (c >> v) & 1 else -1
     return out
+
+
+PROPOSAL_D_IN, PROPOSAL_HIDDEN = 9, 64
+
+
+def proposal_num_params() -> int:
+    """Length of the learned-proposal network's flat parameter vector (9 -> 64 -> 64 -> 1)."""
+    d, h = PROPOSAL_D_IN, PROPOSAL_HIDDEN
+    return d * h + h + h * h + h + h + 1
+
+
+def random_proposal_params(seed: int, scale: float = 0.3) -> np.ndarray:
+    """Random initial parameters [W1, b1, W2, b2, w3, b3] of the proposal network (float64)."""
+    d, h = PROPOSAL_D_IN, PROPOSAL_HIDDEN
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, scale, (d, h))
+    W2 = rng.normal(0, 3 * scale / np.sqrt(h), (h, h))
+    w3 = rng.normal(0, 3 * scale / np.sqrt(h), h)
+    return np.concatenate([W1.ravel(), np.zeros(h), W2.ravel(), np.zeros(h), w3, np.zeros(1)])

@@ -11,10 +11,17 @@
 // then read the accumulator with tcgen05.ld (warp w sees lanes 32*(w%4)..+31, warp
 // group w/4 takes half of the columns), add the bias, apply tanh and store the new rows.
 //
-// Storage: layers 0..L-1 (cached and recomputed) are BF16, as the GEMM consumes them;
-// layer L is FP32, so that Delta log Psi = w_r . sum (h_new - h_old) over the last
-// layer keeps FP32 differences.  Incremental bond groups stack the rows of several
-// antiparallel bonds at the same layer into the same tiles.
+// Storage: cached layers H^0..H^{L-1} are BF16, as the GEMM consumes them; the FP32
+// pre-activations Y^1..Y^L are cached for the incremental step.
+//
+// Incremental ratios propagate differences instead of recomputing rows.  Exchanging
+// s_i and s_j changes layer 0 by dH^0 (rows i and j only).  With X = [A_hat H ; H] and
+// Y = X W + b, layer l changes by dY = [A_hat dH ; dH] W (the bias cancels), nonzero only
+// on ball_l(e), and dH^l = tanh(Y + dY) - tanh(Y) = t (1 - H^2) / (1 + H t) with
+// t = tanh(dY) (the addition formula of tanh), H the cached row.  The GEMM operands are
+// then the small differences themselves, so BF16 rounding is relative to dH rather than
+// to H, and Delta log Psi = w_r[:F] . sum_v dH^L_v accumulates in FP32.  Bond groups
+// stack the rows of several antiparallel bonds at the same layer into the same tiles.
 //
 // Every wait on the mbarrier is bounded: on timeout the kernel records bit 1 in its
 // status word, waits (bounded again) for the MMAs in flight, frees its TMEM and returns.
@@ -152,8 +159,8 @@ struct TcLayout {
   // shared memory byte offsets
   uint32_t oWt, obias, oemb, owr, obr, oA, ospin, oint, odbl, obar, oslot, oregion, smem_total;
   // region (shared or global) byte offsets
-  uint64_t rcache16, rcacheL, rnew16, rnewL, region_bytes;
-  uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's rows (bytes from rnew16)
+  uint64_t rcache16, rY, rnew16, rpart, region_bytes;
+  uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
   int T;                          // A tiles (TMEM holds T accumulators of F columns)
   int G;                          // bonds per group
 };
@@ -205,14 +212,14 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     return x;
   };
   t->rcache16 = rtake((uint64_t)L * N * F * 2);
-  t->rcacheL = rtake((uint64_t)N * F * 4);
+  t->rY = rtake((uint64_t)L * N * F * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
   uint64_t n16 = 0;
   for (int l = 0; l < L; ++l) {
     t->new16_off[l] = n16;
     n16 += (uint64_t)G * maxball[l] * F * 2;
   }
   t->rnew16 = rtake(n16);
-  t->rnewL = rtake((uint64_t)G * maxball[L] * F * 4);
+  t->rpart = rtake((uint64_t)2 * t->T * 128 * 2 * 4);  // [warp group][row][Re, Im] partial Delta
   t->region_bytes = (r + 255) / 256 * 256;
   if (region_in_smem) {
     t->oregion = take(t->region_bytes, 16);
@@ -256,11 +263,15 @@ __device__ __forceinline__ const __nv_bfloat16* cache16(const TcCtx& c, int l) {
 __device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
   return (__nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.F;
 }
-__device__ __forceinline__ float* cacheL(const TcCtx& c) { return (float*)(c.region + c.a->lay.rcacheL); }
+// FP32 pre-activation Y^l (l = 1..L) of every site; for the forward-only call the last
+// slot holds H^L instead.
+__device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
+  return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.F;
+}
 __device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, int l) {
   return (__nv_bfloat16*)(c.region + c.a->lay.rnew16 + c.a->lay.new16_off[l]);
 }
-__device__ __forceinline__ float* newL(const TcCtx& c) { return (float*)(c.region + c.a->lay.rnewL); }
+__device__ __forceinline__ float* dpart(const TcCtx& c) { return (float*)(c.region + c.a->lay.rpart); }
 
 // acc[0..8) += w * bf16 row chunk at p (16 bytes)
 __device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat16* p) {
@@ -306,12 +317,15 @@ __device__ bool run_mmas(TcCtx& c, int nt) {
   return *c.fail == 0;
 }
 
-// Epilogue: rows [0, R) of the nt accumulators -> tanh(acc + b) stored to out (BF16 rows
-// of F, or FP32 rows when out_f32).
-__device__ void epilogue(const TcCtx& c, int nt, int R, void* out, bool out_f32) {
+// Forward epilogue for rows [r0, r0 + R) of layer l: Y = acc + b.  l < L: H^l = tanh(Y)
+// stored BF16 (and Y in FP32 when the call needs the incremental step).  l == L: Y^L in
+// FP32, or, for the forward-only call, H^L = tanh(Y^L) in FP32 for the readout.
+__device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool keep_y) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q4 = warp & 3, wg = warp >> 2;
-  const int F = c.F, half = F / 2;
+  const int F = c.F, half = F / 2, L = c.L;
+  __nv_bfloat16* h16 = l < L ? cache16w(c, l) + (size_t)r0 * F : nullptr;
+  float* y32 = cacheY(c, l) + (size_t)r0 * F;
   for (int t = 0; t < nt; ++t) {
     const int q = t * 128 + q4 * 32 + lane;
     for (int j = 0; j < half / 8; ++j) {
@@ -320,18 +334,25 @@ __device__ void epilogue(const TcCtx& c, int nt, int R, void* out, bool out_f32)
       tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), v);
       if (q < R) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = tanh_fast(v[i] + c.bias[col + i]);
-        if (out_f32) {
-          float4* o = reinterpret_cast<float4*>((float*)out + (size_t)q * F + col);
-          o[0] = make_float4(v[0], v[1], v[2], v[3]);
-          o[1] = make_float4(v[4], v[5], v[6], v[7]);
-        } else {
+        for (int i = 0; i < 8; ++i) v[i] += c.bias[col + i];
+        float4* yo = reinterpret_cast<float4*>(y32 + (size_t)q * F + col);
+        if (l < L) {
+          if (keep_y) {
+            yo[0] = make_float4(v[0], v[1], v[2], v[3]);
+            yo[1] = make_float4(v[4], v[5], v[6], v[7]);
+          }
           uint4 w;
-          w.x = pack_bf16(v[0], v[1]);
-          w.y = pack_bf16(v[2], v[3]);
-          w.z = pack_bf16(v[4], v[5]);
-          w.w = pack_bf16(v[6], v[7]);
-          *reinterpret_cast<uint4*>((__nv_bfloat16*)out + (size_t)q * F + col) = w;
+          w.x = pack_bf16(tanh_fast(v[0]), tanh_fast(v[1]));
+          w.y = pack_bf16(tanh_fast(v[2]), tanh_fast(v[3]));
+          w.z = pack_bf16(tanh_fast(v[4]), tanh_fast(v[5]));
+          w.w = pack_bf16(tanh_fast(v[6]), tanh_fast(v[7]));
+          *reinterpret_cast<uint4*>(h16 + (size_t)q * F + col) = w;
+        } else if (keep_y) {
+          yo[0] = make_float4(v[0], v[1], v[2], v[3]);
+          yo[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+          yo[0] = make_float4(tanhf(v[0]), tanhf(v[1]), tanhf(v[2]), tanhf(v[3]));
+          yo[1] = make_float4(tanhf(v[4]), tanhf(v[5]), tanhf(v[6]), tanhf(v[7]));
         }
       }
     }
@@ -378,10 +399,7 @@ __device__ bool tc_forward(TcCtx& c) {
         *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
       }
       if (!run_mmas(c, nt)) return false;
-      if (l < L)
-        epilogue(c, nt, R, cache16w(c, l) + (size_t)r0 * F, false);
-      else
-        epilogue(c, nt, R, cacheL(c) + (size_t)r0 * F, true);
+      epilogue_fwd(c, nt, R, r0, l, c.a->op == TC_ELOC);
     }
   }
   return true;
@@ -391,7 +409,7 @@ __device__ bool tc_forward(TcCtx& c) {
 __device__ void tc_readout(const TcCtx& c, double out[2]) {
   const int N = c.N, F = c.F;
   float* red = (float*)(c.sdbl + 2 * c.G + 16);
-  const float* HL = cacheL(c);
+  const float* HL = cacheY(c, c.L);  // holds H^L for the forward-only call
   const int parts = blockDim.x / F;
   const int f = threadIdx.x % F, part = threadIdx.x / F;
   if (part < parts) {
@@ -421,50 +439,123 @@ __device__ void tc_readout(const TcCtx& c, double out[2]) {
   __syncthreads();
 }
 
-// Rows of a bond group at layer l: gather into the A tiles.
-__device__ void gather_group(const TcCtx& c, int l, const int* slot_e, int nb, const int* soff) {
+// Slot of group row q at layer l (offsets offl[0..nb]).
+__device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
+  int k = 0;
+  while (k + 1 < nb && offl[k + 1] <= q) ++k;
+  return k;
+}
+
+// dX rows of a bond group at layer l, gathered into the A tiles:
+//   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
+__device__ void gather_delta(const TcCtx& c, int l, const int* slot_e, int nb, const int* soff) {
   const DevGraph& g = c.a->g;
-  const int F = c.F, G = c.G, Lm = g.Lmax;
-  (void)Lm;
+  const int F = c.F, G = c.G;
   const int C8 = (2 * F) / 8, F8 = F / 8;
   const int* offp = soff + (l - 1) * (G + 1);
   const int* offl = soff + l * (G + 1);
   const int R = offl[nb];
-  const __nv_bfloat16* cp = cache16(c, l - 1);
-  const __nv_bfloat16* np = new16(c, l - 1);
+  const __nv_bfloat16* dp = new16(c, l - 1);
   const int items = ((R + 7) / 8) * 8 * C8;
   for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
     const int q8 = idx & 7, ch = (idx >> 3) % C8, qb = (idx >> 3) / C8;
     const int q = qb * 8 + q8;
     if (q >= R) continue;
-    int k = 0;
-    while (k + 1 < nb && offl[k + 1] <= q) ++k;
+    const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
     const int e = slot_e[k];
     const int bo = __ldg(g.ball_off + e);
     const int sprev = offp[k + 1] - offp[k];
-    const __nv_bfloat16* nrow = np + (size_t)offp[k] * F;
-    const int v = __ldg(g.ball_vert + bo + r);
+    const __nv_bfloat16* drow = dp + (size_t)offp[k] * F;
     uint4 outw;
     if (ch < F8) {
       float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const int v = __ldg(g.ball_vert + bo + r);
       const int nb0 = __ldg(g.row_nbr + bo + r);
       const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
       for (int kk = k0; kk < k1; ++kk) {
         const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
-        const __nv_bfloat16* src = p < sprev ? nrow + (size_t)p * F : cp + (size_t)__ldg(g.col + kk) * F;
-        fma_chunk(acc, __ldg(g.wf + kk), src + ch * 8);
+        if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * F + ch * 8);
       }
       outw.x = pack_bf16(acc[0], acc[1]);
       outw.y = pack_bf16(acc[2], acc[3]);
       outw.z = pack_bf16(acc[4], acc[5]);
       outw.w = pack_bf16(acc[6], acc[7]);
+    } else if (r < sprev) {
+      outw = *reinterpret_cast<const uint4*>(drow + (size_t)r * F + (ch - F8) * 8);
     } else {
-      const __nv_bfloat16* src = r < sprev ? nrow + (size_t)r * F : cp + (size_t)v * F;
-      outw = *reinterpret_cast<const uint4*>(src + (ch - F8) * 8);
+      outw = make_uint4(0u, 0u, 0u, 0u);
     }
     *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
   }
+}
+
+// dY in TMEM -> dH = t (1 - H^2) / (1 + H t), t = tanh(dY), for group rows [0, R) at layer
+// l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
+// columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
+__device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e, int nb, const int* soff) {
+  const DevGraph& g = c.a->g;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q4 = warp & 3, wg = warp >> 2;
+  const int F = c.F, half = F / 2, L = c.L, G = c.G;
+  const int* offl = soff + l * (G + 1);
+  const int R = offl[nb];
+  __nv_bfloat16* dout = l < L ? new16(c, l) : nullptr;
+  const float* Yl = cacheY(c, l);
+  float* part = dpart(c);
+  for (int t = 0; t < nt; ++t) {
+    const int q = t * 128 + q4 * 32 + lane;
+    int v = 0;
+    if (q < R) {
+      const int k = slot_of(offl, nb, q);
+      v = __ldg(g.ball_vert + __ldg(g.ball_off + slot_e[k]) + (q - offl[k]));
+    }
+    float pre = 0.f, pim = 0.f;
+    for (int j = 0; j < half / 8; ++j) {
+      const int col = wg * half + j * 8;
+      float dy[8];
+      tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
+      if (q < R) {
+        const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * F + col);
+        const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * F + col + 4);
+        const float y[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float d[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          // e = exp(-2|Y|): H = sgn(Y)(1-e)/(1+e), 1 - H^2 = 4e/(1+e)^2, and
+          // dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t))
+          const float e = __expf(-2.f * fabsf(y[i]));
+          const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
+          const float sg = y[i] < 0.f ? -1.f : 1.f;
+          const float ope = 1.f + e;
+          const float den = ope * (ope + sg * (1.f - e) * tt);
+          // den is small only when the unit swings across saturation: then dH is O(1)
+          // and the direct difference has no cancellation
+          d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(y[i] + dy[i]) - tanhf(y[i]);
+        }
+        if (l < L) {
+          uint4 w;
+          w.x = pack_bf16(d[0], d[1]);
+          w.y = pack_bf16(d[2], d[3]);
+          w.z = pack_bf16(d[4], d[5]);
+          w.w = pack_bf16(d[6], d[7]);
+          *reinterpret_cast<uint4*>(dout + (size_t)q * F + col) = w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            pre += d[i] * c.wr[2 * (col + i)];
+            pim += d[i] * c.wr[2 * (col + i) + 1];
+          }
+        }
+      }
+    }
+    if (l == L && q < R) {
+      part[((size_t)wg * c.T * 128 + q) * 2] = pre;
+      part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
 }
 
 // Incremental Delta log Psi of the bonds slot_e[0..nb): results in sdbl[2k], sdbl[2k+1].
@@ -482,42 +573,32 @@ __device__ bool tc_group(TcCtx& c, const int* slot_e, int nb, int* soff) {
     }
   }
   __syncthreads();
-  // layer 0: the exchanged pair takes each other's embedding rows
-  __nv_bfloat16* n0 = new16(c, 0);
+  // layer 0: dH^0_i = emb(s_j) - emb(s_i), dH^0_j = -dH^0_i
+  __nv_bfloat16* d0 = new16(c, 0);
   for (int i = threadIdx.x; i < nb * 2 * F; i += blockDim.x) {
     const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
     const int e = slot_e[k];
-    const int other = __ldg(g.edges + 2 * e + (1 - r));
-    n0[(size_t)(soff[k] + r) * F + f] = __float2bfloat16_rn(c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f]);
+    const int self = __ldg(g.edges + 2 * e + r), other = __ldg(g.edges + 2 * e + (1 - r));
+    const float dv = c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f] - c.emb[(c.spin[self] > 0 ? 0 : 1) * F + f];
+    d0[(size_t)(soff[k] + r) * F + f] = __float2bfloat16_rn(dv);
   }
   __syncthreads();
   for (int l = 1; l <= L; ++l) {
-    gather_group(c, l, slot_e, nb, soff);
-    const int R = soff[l * (G + 1) + nb];
-    const int nt = (R + 127) / 128;
+    gather_delta(c, l, slot_e, nb, soff);
+    const int nt = (soff[l * (G + 1) + nb] + 127) / 128;
     if (!run_mmas(c, nt)) return false;
-    if (l < L)
-      epilogue(c, nt, R, new16(c, l), false);
-    else
-      epilogue(c, nt, R, newL(c), true);
+    epilogue_delta(c, l, nt, slot_e, nb, soff);
   }
-  // Delta_k = sum_{r in ball_L} (new - old) . w_r[:, k]   (one warp per bond)
+  // Delta_k = sum over the bond's last-layer rows of the per-row partials (one warp per bond)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const float* cL = cacheL(c);
-  const float* nL = newL(c);
   const int* offL = soff + L * (G + 1);
+  const float* part = dpart(c);
+  const size_t wgs = (size_t)c.T * 128;
   for (int k = warp; k < nb; k += nwarps) {
-    const int e = slot_e[k];
-    const int bo = __ldg(g.ball_off + e);
-    const int R = offL[k + 1] - offL[k];
-    const float* nrow = nL + (size_t)offL[k] * F;
     float dre = 0.f, dim = 0.f;
-    for (int i = lane; i < R * F; i += 32) {
-      const int r = i / F, f = i % F;
-      const int v = __ldg(g.ball_vert + bo + r);
-      const float d = nrow[i] - cL[(size_t)v * F + f];
-      dre += d * c.wr[2 * f];
-      dim += d * c.wr[2 * f + 1];
+    for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
+      dre += part[q * 2] + part[(wgs + q) * 2];
+      dim += part[q * 2 + 1] + part[(wgs + q) * 2 + 1];
     }
     dre = warp_sum_t(dre);
     dim = warp_sum_t(dim);

@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--prec", default=os.environ.get("GNA_BENCH_PREC", "auto"))
     p.add_argument("--chains", type=int, default=WORKLOAD["chains"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--only", default=None, choices=["eloc", "eloc_full", "metropolis", "backward", "forward"],
+                   help="time one call of the path alone (for profiling); prints a short JSON line")
     return p.parse_args()
 
 
@@ -433,10 +435,60 @@ def run_ours(a):
     return 0
 
 
+def run_only(a):
+    """One operation of the step alone, W + K launches on the same workload."""
+    import torch
+
+    from paper_2011_12453_gb300 import build as B, gna
+
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    g = W.kagome(6)
+    F, L, C = WORKLOAD["F"], WORKLOAD["L"], a.chains
+    prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32, "auto": gna.PREC_BF16}[a.prec]
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, prec)
+    model32 = gna.Model(F, L, gna.PREC_FP32)
+    theta = torch.tensor(W.random_theta(F, L, 0), dtype=torch.float32, device=dev)
+    spins = torch.tensor(W.random_spins(g.n_sites, C, 1), device=dev)
+    cot = torch.randn(C, 2, dtype=torch.float64, device=dev)
+    out = torch.empty((C, 2), dtype=torch.float64, device=dev)
+
+    def call(k):
+        if a.only == "eloc":
+            gna.local_energy(graph, model, theta, spins, gna.ELOC_INCREMENTAL, out=out)
+        elif a.only == "eloc_full":
+            gna.local_energy(graph, model32, theta, spins, gna.ELOC_FULL, out=out)
+        elif a.only == "forward":
+            gna.forward(graph, model, theta, spins, out=out)
+        elif a.only == "backward":
+            gna.backward(graph, model, theta, spins, cot)
+        else:
+            gna.metropolis_sweep(graph, model, theta, spins, 1, 0, 7, k * g.n_sites)
+
+    for k in range(a.warmup):
+        call(k)
+    torch.cuda.synchronize()
+    ts = []
+    for k in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call(a.warmup + k)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    print(json.dumps({"only": a.only, "prec": a.prec, "chains": C, "ms": ts, "median_ms": float(np.median(ts)),
+                      "samples_per_s": C / (float(np.median(ts)) / 1000.0)}))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.only:
+        return run_only(a)
     return run_ours(a)
 
 

@@ -80,7 +80,8 @@ typedef enum {
   GNA_OP_METROPOLIS = 3,
   GNA_OP_BACKWARD = 4,
   GNA_OP_ISGO_WEIGHTS = 5,
-  GNA_OP_ISGO_GRAD = 6
+  GNA_OP_ISGO_GRAD = 6,
+  GNA_OP_METROPOLIS_LEARNED = 7 /* gna_metropolis_sweep with a proposal network */
 } gna_op;
 
 /* Model description (Eq. gcn).  F = embedding width, L = number of GCN layers,
@@ -178,25 +179,39 @@ GNA_API gna_status gna_local_energy(const gna_graph* g, const gna_model_desc* d,
                             float* dlogpsi_bonds, void* workspace, size_t workspace_bytes,
                             void* stream);
 
-/* Metropolis pair-exchange sweeps sampling P ~ |Psi|^2 (scaling section), one chain per
- * row.  Step t of chain c draws (r0, r1, r2, r3) = Philox4x64-10(key = (seed, c),
- * counter = (t, 0, 0, 0)) (Salmon et al., SC'11), proposes bond e = hi64(r0 * n_edges),
- * rejects if s_i == s_j, else accepts the exchange iff u < exp(2 Re(log Psi(s^e) -
- * log Psi(s))) with u = (r1 >> 11) 2^-53 (FP64) or (r1 >> 40) 2^-24 (FP32/BF16).
+/* Metropolis(-Hastings) pair-exchange sweeps sampling P ~ |Psi|^2 (scaling section), one
+ * chain per row.  Step t of chain c draws (r0, r1, r2, r3) = Philox4x64-10(key = (seed,
+ * c), counter = (t, 0, 0, 0)) (Salmon et al., SC'11).
+ *   Plain moves (proposal_params == NULL): bond e = hi64(r0 * n_edges); a parallel bond
+ *   is a rejected step; else the exchange is accepted iff
+ *   u < exp(2 Re(log Psi(s^e) - log Psi(s))), u = (r1 >> 11) 2^-53 (FP64) or
+ *   (r1 >> 40) 2^-24 (FP32/BF16).
+ *   Learned moves (proposal_params != NULL, network of gna_proposal_logits): with
+ *   probability proposal_eps ((r3 >> 40) 2^-24 < eps) the step is a plain bond move;
+ *   otherwise site i = hi64(r2 * n_sites) and its partner j is drawn from the softmax of
+ *   the network's logits over i's antiparallel neighbours (uniform (r3 mod 2^32) 2^-32,
+ *   neighbours in adjacency order; none: rejected step).  Either way the exchange of
+ *   {i, j} is accepted iff u < exp(2 Re Delta) q(s'->s)/q(s->s') with the exact mixture
+ *   density q(s->s') = (1-eps)/N [pi_i(j|s) + pi_j(i|s)] + eps/n_edges, so |Psi|^2 stays
+ *   stationary.  Needs a graph of maximum degree <= 16.
  * Steps run for t = step0 .. step0 + n_sweeps*n_sites - 1.
  *   chain_spins  dev int8 [C][n_sites], read and updated in place (S_z is conserved)
  *   record_every  0 = no records; k > 0 = record after every k-th sweep
+ *   proposal_params dev float32 [gna_proposal_num_params()] or NULL; proposal_eps in [0, 1]
  *   samples_out  dev int8 [n_sweeps/record_every][C][n_sites] or NULL
  *   logpsi_out   dev float64 [n_sweeps/record_every][C][2] or NULL: log Psi of each
  *                record, recomputed from the chain's state at the record
  *   n_accepted   dev int32 [C] or NULL: incremented by the number of accepted moves
- *   trace        dev float64 [C][n_sweeps*n_sites][3] or NULL: per step (bond, accepted,
- *                Re Delta or NaN for a parallel bond), for decision-parity checks
+ *   trace        dev float64 [C][n_sweeps*n_sites][4] or NULL: per step (bond or -1,
+ *                accepted, value, kind) with value = Re Delta (plain sampler) or the log
+ *                acceptance ratio (with a proposal network), NaN when nothing was
+ *                proposed, and kind 1 = plain bond, 2 = network move
  * Incremental ratios are computed in d->prec (BF16 runs the FP32 sampler). */
 GNA_API gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_desc* d,
                                 const void* theta, int8_t* chain_spins, int64_t C,
                                 int32_t n_sweeps, int32_t record_every, uint64_t seed,
-                                uint64_t step0, int8_t* samples_out, double* logpsi_out,
+                                uint64_t step0, const float* proposal_params,
+                                double proposal_eps, int8_t* samples_out, double* logpsi_out,
                                 int32_t* n_accepted, double* trace, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
@@ -265,6 +280,36 @@ GNA_API gna_status isgo_grad(const gna_graph* g, const gna_model_desc* d, const 
 /* Plain gradient step w <- w - lr * grad (scaling section).  theta typed as above. */
 GNA_API gna_status gna_sgd_update(const gna_model_desc* d, void* theta, const double* grad,
                           double lr, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Learned exchange proposal (not in the paper: a proposal for its MCMC step).
+ * Network 9 -> 64 -> 64 -> 1 with tanh hidden units on the features of an ordered pair
+ * (i, j): s_i, s_j, J_ij, 1/d_i, 1/d_j, the mean spin of i's other neighbours, that of
+ * j's, and the mean over i's (j's) other neighbours u of their neighbour-spin mean.
+ * Flat float32 parameters [W1 (9 x 64), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3].
+ * ------------------------------------------------------------------------------- */
+GNA_API int32_t gna_proposal_num_params(void);
+GNA_API gna_status gna_proposal_workspace_size(const gna_graph* g, int64_t B, size_t* bytes);
+
+/* Logits of every (configuration, bond, orientation): logits dev float32 [B][n_edges][2],
+ * orientation 0 scores edges[e][0] -> edges[e][1]; NaN for parallel bonds. */
+GNA_API gna_status gna_proposal_logits(const gna_graph* g, const int8_t* spins, int64_t B,
+                                       const float* params, float* logits, void* stream);
+
+/* Gradient of the training loss: mean over both orientations of every antiparallel bond
+ * of (logit - min(0, 2 dlogpsi_bonds[b][e]))^2, the log acceptance of the plain move.
+ *   dlogpsi_bonds dev float32 [B][n_edges] (from gna_local_energy)
+ *   grad dev float64 [num_params]; loss dev float64 [1] or NULL
+ * Per-block partials reduced in float64 in a fixed order. */
+GNA_API gna_status gna_proposal_grad(const gna_graph* g, const int8_t* spins,
+                                     const float* dlogpsi_bonds, int64_t B, const float* params,
+                                     double* grad, double* loss, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on the float32
+ * parameters with float32 moments m, v; t >= 1 is the step number. */
+GNA_API gna_status gna_proposal_adam(float* params, float* m, float* v, const double* grad,
+                                     int32_t t, double lr, void* stream);
 
 /* Philox4x64-10 blocks of the sampler's generator, for bit-exact checks.
  *   keys dev uint64 [n][2]; counters dev uint64 [n][4]; out dev uint64 [n][4]. */

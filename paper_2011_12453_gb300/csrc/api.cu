@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "prop.cuh"
 #include "tc.cuh"
 
 namespace gna {
@@ -121,6 +122,9 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       return simt_workspace(g, m, sp, 2, B, bytes);
     case GNA_OP_METROPOLIS:
       return simt_workspace(g, m, sp, 3, B, bytes);
+    case GNA_OP_METROPOLIS_LEARNED:
+      if (g->max_deg > 16) return GNA_ERR_UNSUPPORTED;
+      return simt_workspace(g, m, sp, 5, B, bytes);
     case GNA_OP_BACKWARD:
       return simt_workspace(g, m, sp, 4, B, bytes);
     case GNA_OP_ISGO_WEIGHTS:
@@ -220,7 +224,8 @@ extern "C" gna_status gna_local_energy(const gna_graph* g, const gna_model_desc*
 
 extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_desc* d, const void* theta,
                                            int8_t* chain_spins, int64_t C, int32_t n_sweeps, int32_t record_every,
-                                           uint64_t seed, uint64_t step0, int8_t* samples_out, double* logpsi_out,
+                                           uint64_t seed, uint64_t step0, const float* proposal_params,
+                                           double proposal_eps, int8_t* samples_out, double* logpsi_out,
                                            int32_t* n_accepted, double* trace, void* workspace,
                                            size_t workspace_bytes, void* stream) {
   gna_status st = check_gd(g, d);
@@ -230,7 +235,8 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
   if (g->d.E < 1) return GNA_ERR_INVALID_ARG;  // no bond to propose
   if (!theta || !chain_spins) return GNA_ERR_INVALID_ARG;
   if (record_every > 0 && n_sweeps / record_every > 0 && !samples_out && !logpsi_out) return GNA_ERR_INVALID_ARG;
-  st = check_ws(g, d, GNA_OP_METROPOLIS, C, workspace, workspace_bytes);
+  if (proposal_params && !(proposal_eps >= 0.0 && proposal_eps <= 1.0)) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, proposal_params ? GNA_OP_METROPOLIS_LEARNED : GNA_OP_METROPOLIS, C, workspace, workspace_bytes);
   if (st != GNA_OK) return st;
   SimtCall sc{};
   sc.g = g;
@@ -247,6 +253,8 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
   sc.logpsi_out = logpsi_out;
   sc.n_acc = n_accepted;
   sc.trace = trace;
+  sc.prop = proposal_params;
+  sc.prop_eps = proposal_eps;
   return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
@@ -334,6 +342,50 @@ extern "C" gna_status gna_sgd_update(const gna_model_desc* d, void* theta, const
                                      void* stream) {
   if (!desc_ok(d) || !theta || !grad || !std::isfinite(lr)) return GNA_ERR_INVALID_ARG;
   return sgd_launch(d->prec, theta, grad, lr, (int)gna_num_params(d), (cudaStream_t)stream);
+}
+
+extern "C" int32_t gna_proposal_num_params(void) { return kPropParams; }
+
+static gna_status check_graph(const gna_graph* g) {
+  if (!g) return GNA_ERR_INVALID_ARG;
+  int dev = 0;
+  GNA_CUDA_TRY(cudaGetDevice(&dev));
+  return dev == g->device ? GNA_OK : GNA_ERR_INVALID_ARG;
+}
+
+extern "C" gna_status gna_proposal_workspace_size(const gna_graph* g, int64_t B, size_t* bytes) {
+  gna_status st = check_graph(g);
+  if (st != GNA_OK) return st;
+  if (!bytes || B < 0) return GNA_ERR_INVALID_ARG;
+  *bytes = B == 0 ? 0 : prop_workspace(g, B);
+  return GNA_OK;
+}
+
+extern "C" gna_status gna_proposal_logits(const gna_graph* g, const int8_t* spins, int64_t B, const float* params,
+                                          float* logits, void* stream) {
+  gna_status st = check_graph(g);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (B == 0 || g->d.E == 0) return GNA_OK;
+  if (!spins || !params || !logits) return GNA_ERR_INVALID_ARG;
+  return prop_logits_launch(g, spins, B, params, logits, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_proposal_grad(const gna_graph* g, const int8_t* spins, const float* dlogpsi_bonds,
+                                        int64_t B, const float* params, double* grad, double* loss, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+  gna_status st = check_graph(g);
+  if (st != GNA_OK) return st;
+  if (B < 1 || B > (int64_t)1 << 31 || g->d.E == 0) return GNA_ERR_INVALID_ARG;
+  if (!spins || !dlogpsi_bonds || !params || !grad) return GNA_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < prop_workspace(g, B)) return GNA_ERR_WORKSPACE;
+  return prop_grad_launch(g, spins, dlogpsi_bonds, B, params, grad, loss, workspace, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_proposal_adam(float* params, float* m, float* v, const double* grad, int32_t t, double lr,
+                                        void* stream) {
+  if (!params || !m || !v || !grad || t < 1 || !std::isfinite(lr)) return GNA_ERR_INVALID_ARG;
+  return prop_adam_launch(params, m, v, grad, t, lr, (cudaStream_t)stream);
 }
 
 extern "C" gna_status gna_philox4x64_10(const uint64_t* keys, const uint64_t* counters, int64_t n, uint64_t* out,

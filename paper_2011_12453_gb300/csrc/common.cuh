@@ -19,6 +19,7 @@ struct DevGraph {
   int n = 0, E = 0, Lmax = 0;
   const int* row_ptr = nullptr;   // [n+1]
   const int* col = nullptr;       // [2E]   neighbour u of v at row_ptr[v]..row_ptr[v+1]
+  const int* col_edge = nullptr;  // [2E]   bond index of that CSR entry
   const float* wf = nullptr;      // [2E]   1/sqrt(d_v d_u), float32
   const double* wd = nullptr;     // [2E]   same, float64
   const int* edges = nullptr;     // [E][2]
@@ -41,6 +42,7 @@ struct gna_graph {
   std::vector<int> h_row_ptr, h_col, h_edges, h_ball_size, h_ball_off;
   std::vector<double> h_J;
   std::vector<int> max_ball;  // [Lmax+1] max over bonds of |ball_l|
+  int max_deg = 0;
   std::vector<void*> allocations;
 };
 
@@ -113,6 +115,8 @@ struct SimtCall {
   double* logpsi_out = nullptr;
   int32_t* n_acc = nullptr;
   double* trace = nullptr;
+  const float* prop = nullptr;  // learned proposal parameters (Metropolis) or NULL
+  double prop_eps = 0.0;
 };
 
 // Entry points of the translation units.
@@ -176,6 +180,7 @@ struct Plan {
   size_t ws_bytes = 0;     // workspace bytes for the whole launch
   int G = 1;               // bonds processed together (local energy)
   int partial_in_smem = 0; // backward: per-CTA gradient partial in shared memory
+  int prop_rows = 0;       // Metropolis with a proposal network: row buffer capacity
 };
 
 }  // namespace gna

@@ -1,6 +1,7 @@
 // Graph handle: CSR adjacency, normalised weights of D^-1/2 A D^-1/2 (Eq. gcn) and the
 // nested bond neighbourhoods that bound the rows an exchange of s_i, s_j can change at
 // each GCN layer.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -16,7 +17,7 @@ namespace {
 
 struct HostGraph {
   int n = 0, E = 0, Lmax = 0;
-  std::vector<int> row_ptr, col, edges;
+  std::vector<int> row_ptr, col, col_edge, edges;
   std::vector<float> wf;
   std::vector<double> wd, J;
   std::vector<int> ball_off, ball_size, ball_vert, row_nbr, nbr_pos, max_ball;
@@ -52,11 +53,14 @@ void build(int n, int E, const int32_t* edges, const double* J, int Lmax, HostGr
   h->row_ptr.assign(n + 1, 0);
   for (int v = 0; v < n; ++v) h->row_ptr[v + 1] = h->row_ptr[v] + deg[v];
   h->col.assign(2 * E, 0);
+  h->col_edge.assign(2 * E, 0);
   std::vector<int> fill(h->row_ptr.begin(), h->row_ptr.end() - 1);
   // neighbours in edge-list order
   for (int e = 0; e < E; ++e) {
     int a = edges[2 * e], b = edges[2 * e + 1];
+    h->col_edge[fill[a]] = e;
     h->col[fill[a]++] = b;
+    h->col_edge[fill[b]] = e;
     h->col[fill[b]++] = a;
   }
   h->wf.resize(2 * E);
@@ -163,6 +167,7 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   }
   UP(h.row_ptr, row_ptr);
   UP(h.col, col);
+  UP(h.col_edge, col_edge);
   UP(h.wf, wf);
   UP(h.wd, wd);
   UP(h.edges, edges);
@@ -180,6 +185,7 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   g->h_ball_off = h.ball_off;
   g->h_J = h.J;
   g->max_ball = h.max_ball;
+  for (int v = 0; v < h.n; ++v) g->max_deg = std::max(g->max_deg, h.row_ptr[v + 1] - h.row_ptr[v]);
   *out = g;
   return GNA_OK;
 }

@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "prop.cuh"
 
 namespace gna {
 
@@ -42,7 +43,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ---------------------------------------------------------------------------------
 // kernel arguments and shared-memory carve (same arithmetic on host and device)
 // ---------------------------------------------------------------------------------
-enum SimtOp { OP_FWD = 0, OP_ELOC_FULL = 1, OP_ELOC_INCR = 2, OP_METRO = 3, OP_BWD = 4 };
+enum SimtOp { OP_FWD = 0, OP_ELOC_FULL = 1, OP_ELOC_INCR = 2, OP_METRO = 3, OP_BWD = 4, OP_METRO_LEARNED = 5 };
 
 template <typename T>
 struct SimtArgs {
@@ -69,10 +70,14 @@ struct SimtArgs {
   T* gregion;  // [grid][region_elems] when the region is not in shared memory
   size_t region_elems;
   int region_in_smem, partial_in_smem;
+  // learned exchange proposal (Metropolis only): network parameters or NULL
+  const float* prop;
+  double prop_eps;
+  int prop_rows;  // capacity of the per-step row buffer (4 x max degree)
 };
 
 struct Carve {
-  size_t oW, ob, oemb, owr, obr, ospin, oint, odbl, opart, oregion, total;
+  size_t oW, ob, oemb, owr, obr, ospin, oint, odbl, opart, oprop, ophi, oh1, oh2, ologit, orow, oregion, total;
 };
 
 // ints: bond list [E] + slot bonds [G] + row offsets [(L+1)][G+1] + misc 16
@@ -81,7 +86,7 @@ __host__ __device__ inline size_t carve_ints(int E, int G, int L) {
 }
 
 __host__ __device__ inline Carve carve(const Dims& m, int G, size_t sizeT, int part_smem,
-                                       size_t region_elems_smem) {
+                                       size_t region_elems_smem, int prop_rows = 0) {
   Carve c;
   const int F = m.F, ldw = F + 1;
   size_t o = 0;
@@ -99,6 +104,13 @@ __host__ __device__ inline Carve carve(const Dims& m, int G, size_t sizeT, int p
   c.oint = take(carve_ints(m.E, G, m.L) * 4);
   c.odbl = take((size_t)(2 * G + 2 * kThreads + 8) * 8);
   c.opart = take(part_smem ? (size_t)m.P * 8 : 0);
+  const size_t pr = (size_t)prop_rows;
+  c.oprop = take(pr ? (size_t)kPropParams * sizeT : 0);
+  c.ophi = take(pr * (kPropIn + 1) * sizeT);
+  c.oh1 = take(pr * (kPropHid + 1) * sizeT);
+  c.oh2 = take(pr * (kPropHid + 1) * sizeT);
+  c.ologit = take(pr * sizeT);
+  c.orow = take(pr * 3 * 4);
   c.oregion = take(region_elems_smem * sizeT);
   c.total = o;
   return c;
@@ -116,7 +128,8 @@ __host__ __device__ inline size_t region_elems(int op, const Dims& m, int G, con
     case OP_ELOC_FULL:
       return 3 * NF;  // H (N x F) + X (N x 2F)
     case OP_ELOC_INCR:
-    case OP_METRO: {
+    case OP_METRO:
+    case OP_METRO_LEARNED: {
       size_t newrows = 0;
       for (int l = 0; l <= m.L; ++l) newrows += (size_t)G * maxball[l];
       return (size_t)(m.L + 1) * NF + newrows * m.F + xrows_incr(m, G, maxball) * 2 * m.F;
@@ -140,6 +153,9 @@ struct Ctx {
   double* sdbl;
   double* part;  // gradient partial [P]
   T* region;
+  // learned proposal buffers
+  T *pW, *phi, *h1, *h2, *logit;
+  int* rows;  // [prop_rows][3]: centre i, other j, 1 if evaluated in the exchanged state
 };
 
 template <typename T>
@@ -150,7 +166,7 @@ __device__ inline void make_ctx(const SimtArgs<T>& a, Ctx<T>& c, unsigned char* 
   c.L = a.m.L;
   c.E = a.m.E;
   c.ldw = a.m.F + 1;
-  Carve cv = carve(a.m, a.G, sizeof(T), a.partial_in_smem, a.region_in_smem ? a.region_elems : 0);
+  Carve cv = carve(a.m, a.G, sizeof(T), a.partial_in_smem, a.region_in_smem ? a.region_elems : 0, a.prop_rows);
   c.sW = (T*)(smem + cv.oW);
   c.sb = (T*)(smem + cv.ob);
   c.semb = (T*)(smem + cv.oemb);
@@ -162,6 +178,12 @@ __device__ inline void make_ctx(const SimtArgs<T>& a, Ctx<T>& c, unsigned char* 
   c.sdbl = (double*)(smem + cv.odbl);
   c.part = a.partial_in_smem ? (double*)(smem + cv.opart) : a.partial + (size_t)blockIdx.x * a.m.P;
   c.region = a.region_in_smem ? (T*)(smem + cv.oregion) : a.gregion + (size_t)blockIdx.x * a.region_elems;
+  c.pW = (T*)(smem + cv.oprop);
+  c.phi = (T*)(smem + cv.ophi);
+  c.h1 = (T*)(smem + cv.oh1);
+  c.h2 = (T*)(smem + cv.oh2);
+  c.logit = (T*)(smem + cv.ologit);
+  c.rows = (int*)(smem + cv.orow);
 }
 
 // Weights of GCN layer l (0-based) into shared memory, W with padded row stride F+1.
@@ -428,6 +450,125 @@ __device__ void incr_group(const Ctx<T>& c, const IncrLayout<T>& lay, const int8
   __syncthreads();
 }
 
+
+// ---------------------------------------------------------------------------------
+// learned exchange proposal inside the sampler
+// ---------------------------------------------------------------------------------
+// Spin of site v in s, or in s with the pair (a, b) exchanged when a >= 0.
+__device__ __forceinline__ int spin_at(const int8_t* sp, int v, int a, int b) {
+  return v == a ? sp[b] : (v == b ? sp[a] : sp[v]);
+}
+
+template <typename T>
+__device__ T nbr_sum(const DevGraph& g, const int8_t* sp, int v, int a, int b) {
+  T acc = 0;
+  const int k1 = __ldg(g.row_ptr + v + 1);
+  for (int k = __ldg(g.row_ptr + v); k < k1; ++k) acc += (T)spin_at(sp, __ldg(g.col + k), a, b);
+  return acc;
+}
+
+// Logits of the rows c.rows[0..nrows): row (i, j, x) scores the exchange i -> j in s
+// (x = 0) or in s with (pi, pj) exchanged (x = 1).  CTA-cooperative.
+template <typename T>
+__device__ void prop_logits(const Ctx<T>& c, const int8_t* sp, int nrows, int pi, int pj) {
+  const DevGraph& g = c.a->g;
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const int i = c.rows[3 * r], j = c.rows[3 * r + 1];
+    const int a = c.rows[3 * r + 2] ? pi : -1, b = c.rows[3 * r + 2] ? pj : -1;
+    const int ki0 = __ldg(g.row_ptr + i), ki1 = __ldg(g.row_ptr + i + 1);
+    const int kj0 = __ldg(g.row_ptr + j), kj1 = __ldg(g.row_ptr + j + 1);
+    const int di = ki1 - ki0, dj = kj1 - kj0;
+    const T si = (T)spin_at(sp, i, a, b), sj = (T)spin_at(sp, j, a, b);
+    T Jij = 0, bi = 0, bj = 0;
+    int ci = 0, cj = 0;
+    for (int k = ki0; k < ki1; ++k) {
+      const int u = __ldg(g.col + k);
+      if (u == j) {
+        Jij = (T)__ldg(g.J + __ldg(g.col_edge + k));
+        continue;
+      }
+      bi += nbr_sum<T>(g, sp, u, a, b) / (T)(__ldg(g.row_ptr + u + 1) - __ldg(g.row_ptr + u));
+      ++ci;
+    }
+    for (int k = kj0; k < kj1; ++k) {
+      const int u = __ldg(g.col + k);
+      if (u == i) continue;
+      bj += nbr_sum<T>(g, sp, u, a, b) / (T)(__ldg(g.row_ptr + u + 1) - __ldg(g.row_ptr + u));
+      ++cj;
+    }
+    T* f = c.phi + r * (kPropIn + 1);
+    f[0] = si;
+    f[1] = sj;
+    f[2] = Jij;
+    f[3] = (T)1 / (T)di;
+    f[4] = (T)1 / (T)dj;
+    f[5] = (nbr_sum<T>(g, sp, i, a, b) - sj) / (T)max(di - 1, 1);
+    f[6] = (nbr_sum<T>(g, sp, j, a, b) - si) / (T)max(dj - 1, 1);
+    f[7] = ci ? bi / (T)ci : (T)0;
+    f[8] = cj ? bj / (T)cj : (T)0;
+  }
+  __syncthreads();
+  const T* W1 = c.pW + kPropOW1;
+  const T* b1 = c.pW + kPropOb1;
+  const T* W2 = c.pW + kPropOW2;
+  const T* b2 = c.pW + kPropOb2;
+  const T* w3 = c.pW + kPropOw3;
+  for (int idx = threadIdx.x; idx < nrows * kPropHid; idx += blockDim.x) {
+    const int r = idx / kPropHid, k = idx % kPropHid;
+    T z = b1[k];
+    for (int f = 0; f < kPropIn; ++f) z += c.phi[r * (kPropIn + 1) + f] * W1[f * kPropHid + k];
+    c.h1[r * (kPropHid + 1) + k] = f_tanh(z);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nrows * kPropHid; idx += blockDim.x) {
+    const int r = idx / kPropHid, k = idx % kPropHid;
+    T z = b2[k];
+    for (int mm = 0; mm < kPropHid; ++mm) z += c.h1[r * (kPropHid + 1) + mm] * W2[mm * kPropHid + k];
+    c.h2[r * (kPropHid + 1) + k] = f_tanh(z);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < nrows; r += blockDim.x >> 5) {
+    T z = c.h2[r * (kPropHid + 1) + lane] * w3[lane] + c.h2[r * (kPropHid + 1) + lane + 32] * w3[lane + 32];
+    z = warp_sum(z);
+    if (lane == 0) c.logit[r] = z + c.pW[kPropOb3];
+  }
+  __syncthreads();
+}
+
+// Appends the rows (i -> u) for the antiparallel neighbours u of i (in CSR order), in s
+// or in the exchanged state; returns the new row count (thread 0 only).
+template <typename T>
+__device__ int push_candidates(const Ctx<T>& c, const int8_t* sp, int i, int swapped, int pi, int pj, int n) {
+  const DevGraph& g = c.a->g;
+  const int a = swapped ? pi : -1, b = swapped ? pj : -1;
+  const int si = spin_at(sp, i, a, b);
+  for (int k = __ldg(g.row_ptr + i); k < __ldg(g.row_ptr + i + 1); ++k) {
+    const int u = __ldg(g.col + k);
+    if (spin_at(sp, u, a, b) != si) {
+      c.rows[3 * n] = i;
+      c.rows[3 * n + 1] = u;
+      c.rows[3 * n + 2] = swapped;
+      ++n;
+    }
+  }
+  return n;
+}
+
+// Softmax probability of the row for (i -> target) among the rows [r0, r1) (thread 0).
+template <typename T>
+__device__ T softmax_prob(const Ctx<T>& c, int r0, int r1, int target) {
+  T zmax = c.logit[r0];
+  for (int r = r0 + 1; r < r1; ++r) zmax = c.logit[r] > zmax ? c.logit[r] : zmax;
+  T sum = 0, pt = 0;
+  for (int r = r0; r < r1; ++r) {
+    const T w = f_exp(c.logit[r] - zmax);
+    sum += w;
+    if (c.rows[3 * r + 1] == target) pt = w;
+  }
+  return pt / sum;
+}
+
 // ---------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------
@@ -571,20 +712,38 @@ __device__ inline bool metropolis_accept<float>(uint64_t r1, double dre) {
 }
 
 template <typename T>
+__device__ inline bool accept_log(uint64_t r1, T log_ratio);
+template <>
+__device__ inline bool accept_log<double>(uint64_t r1, double log_ratio) {
+  return (double)(r1 >> 11) * 0x1.0p-53 < exp(log_ratio);
+}
+template <>
+__device__ inline bool accept_log<float>(uint64_t r1, float log_ratio) {
+  return (float)(r1 >> 40) * 0x1.0p-24f < expf(log_ratio);
+}
+
+// Metropolis(-Hastings) pair-exchange sweeps, one chain per CTA at a time.  Without a
+// proposal network every step proposes a uniform bond; with one, a step is a plain bond
+// with probability eps, else site i uniform and its partner drawn from the network's
+// softmax over i's antiparallel neighbours, accepted with the exact proposal ratio.
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_metropolis(const SimtArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctx<T> c;
   make_ctx(a, c, smem);
   load_fixed(c);
+  if (a.prop)
+    for (int i = threadIdx.x; i < kPropParams; i += blockDim.x) c.pW[i] = (T)a.prop[i];
   const IncrLayout<T> lay = incr_layout(c);
   int* slot_e = c.sint + c.E;
   int* soff = slot_e + a.G;
   const size_t NF = (size_t)c.N * c.F;
   const int64_t n_steps = (int64_t)a.n_sweeps * c.N;
   const int n_rec = a.record_every > 0 ? a.n_sweeps / a.record_every : 0;
-  __shared__ int s_acc_flag;
-  __shared__ int s_accepts;
-  __shared__ uint64_t s_r1;
+  const T eps = (T)a.prop_eps;
+  __shared__ int s_acc_flag, s_accepts, s_kind, s_move, s_i, s_j, s_n, s_grp[5];
+  __shared__ uint64_t s_r1, s_r3;
+  __shared__ T s_pij, s_logq;
   for (int64_t ch = blockIdx.x; ch < a.B; ch += gridDim.x) {
     for (int i = threadIdx.x; i < c.N; i += blockDim.x) c.sspin[i] = a.chain_spins[ch * c.N + i];
     if (threadIdx.x == 0) s_accepts = 0;
@@ -593,32 +752,115 @@ __global__ void __launch_bounds__(kThreads) k_metropolis(const SimtArgs<T> a) {
     for (int64_t k = 0; k < n_steps; ++k) {
       if (threadIdx.x == 0) {
         const U64x4 w = philox4x64_10(a.seed, (uint64_t)ch, U64x4{a.step0 + (uint64_t)k, 0, 0, 0});
-        slot_e[0] = (int)__umul64hi(w.x, (uint64_t)c.E);
         s_r1 = w.y;
+        s_r3 = w.w;
         s_acc_flag = 0;
+        s_logq = 0;
+        bool plain = true;
+        if (a.prop) plain = (double)(w.w >> 40) * 0x1.0p-24 < a.prop_eps;
+        if (plain) {
+          const int e = (int)__umul64hi(w.x, (uint64_t)c.E);
+          slot_e[0] = e;
+          s_i = __ldg(a.g.edges + 2 * e);
+          s_j = __ldg(a.g.edges + 2 * e + 1);
+          s_kind = 1;
+          s_move = c.sspin[s_i] != c.sspin[s_j];
+        } else {
+          s_kind = 2;
+          s_i = (int)__umul64hi(w.z, (uint64_t)c.N);
+          s_j = -1;
+          slot_e[0] = -1;
+          s_n = push_candidates(c, c.sspin, s_i, 0, -1, -1, 0);
+          s_move = s_n > 0;
+        }
       }
       __syncthreads();
+      if (s_kind == 2 && s_move) {
+        // round 1: the partner j of i drawn from pi_i(. | s)
+        prop_logits(c, c.sspin, s_n, -1, -1);
+        if (threadIdx.x == 0) {
+          const int n = s_n;
+          T zmax = c.logit[0];
+          for (int r = 1; r < n; ++r) zmax = c.logit[r] > zmax ? c.logit[r] : zmax;
+          T sum = 0;
+          for (int r = 0; r < n; ++r) sum += f_exp(c.logit[r] - zmax);
+          const T uc = (T)((double)(s_r3 & 0xFFFFFFFFull) * 0x1.0p-32);
+          T cum = 0;
+          int pick = n - 1;
+          for (int r = 0; r < n; ++r) {
+            cum += f_exp(c.logit[r] - zmax) / sum;
+            if (uc < cum) {
+              pick = r;
+              break;
+            }
+          }
+          s_j = c.rows[3 * pick + 1];
+          s_pij = f_exp(c.logit[pick] - zmax) / sum;
+          for (int kk = __ldg(a.g.row_ptr + s_i); kk < __ldg(a.g.row_ptr + s_i + 1); ++kk)
+            if (__ldg(a.g.col + kk) == s_j) slot_e[0] = __ldg(a.g.col_edge + kk);
+        }
+        __syncthreads();
+      }
       const int e = slot_e[0];
-      const int i = __ldg(a.g.edges + 2 * e), j = __ldg(a.g.edges + 2 * e + 1);
-      const bool anti = c.sspin[i] != c.sspin[j];
-      double* tr = a.trace ? a.trace + ((size_t)ch * n_steps + k) * 3 : nullptr;
-      if (!anti) {
+      const int i = s_i, j = s_j;
+      double* tr = a.trace ? a.trace + ((size_t)ch * n_steps + k) * 4 : nullptr;
+      if (!s_move) {
         if (tr && threadIdx.x == 0) {
           tr[0] = (double)e;
           tr[1] = 0.0;
           tr[2] = __longlong_as_double(0x7ff8000000000000ll);
+          tr[3] = (double)s_kind;
         }
       } else {
+        if (a.prop) {
+          // the exact mixture proposal density both ways: q(s -> s') and q(s' -> s)
+          if (threadIdx.x == 0) {
+            int n = 0;
+            s_grp[0] = 0;
+            if (s_kind == 1) n = push_candidates(c, c.sspin, i, 0, i, j, n);
+            s_grp[1] = n;
+            n = push_candidates(c, c.sspin, j, 0, i, j, n);
+            s_grp[2] = n;
+            n = push_candidates(c, c.sspin, i, 1, i, j, n);
+            s_grp[3] = n;
+            n = push_candidates(c, c.sspin, j, 1, i, j, n);
+            s_grp[4] = n;
+            s_n = n;
+          }
+          __syncthreads();
+          prop_logits(c, c.sspin, s_n, i, j);
+          if (threadIdx.x == 0) {
+            const T pij = s_kind == 1 ? softmax_prob(c, s_grp[0], s_grp[1], j) : s_pij;
+            const T pji = softmax_prob(c, s_grp[1], s_grp[2], i);
+            const T pij2 = softmax_prob(c, s_grp[2], s_grp[3], j);
+            const T pji2 = softmax_prob(c, s_grp[3], s_grp[4], i);
+            const T w_learn = ((T)1 - eps) / (T)c.N, w_plain = eps / (T)c.E;
+            const T qf = w_learn * (pij + pji) + w_plain;
+            const T qr = w_learn * (pij2 + pji2) + w_plain;
+            s_logq = (T)(log((double)qr) - log((double)qf));
+          }
+          __syncthreads();
+        }
         incr_group(c, lay, c.sspin, slot_e, 1, soff);
         if (threadIdx.x == 0) {
           const double dre = c.sdbl[0];
-          const int acc = metropolis_accept<T>(s_r1, dre) ? 1 : 0;
+          int acc;
+          double value;
+          if (a.prop) {
+            const T lr = (T)2 * (T)dre + s_logq;
+            acc = accept_log<T>(s_r1, lr) ? 1 : 0;
+            value = (double)lr;
+          } else {
+            acc = metropolis_accept<T>(s_r1, dre) ? 1 : 0;
+            value = dre;
+          }
           s_acc_flag = acc;
           s_accepts += acc;
           if (tr) {
             tr[0] = (double)e;
             tr[1] = (double)acc;
-            tr[2] = dre;
+            tr[2] = value;
+            tr[3] = (double)s_kind;
           }
         }
         __syncthreads();
@@ -810,6 +1052,7 @@ static const void* kernel_ptr(int op) {
     case OP_ELOC_INCR:
       return (const void*)k_eloc_incr<T>;
     case OP_METRO:
+    case OP_METRO_LEARNED:
       return (const void*)k_metropolis<T>;
     case OP_BWD:
       return (const void*)k_backward<T>;
@@ -826,6 +1069,8 @@ gna_status simt_plan(const gna_graph* g, const Dims& m, int op, int64_t B, Plan*
   int maxball[kMaxL + 1] = {0};
   for (int l = 0; l <= m.L && l <= g->d.Lmax; ++l) maxball[l] = mb[l];
   const int part = (op == OP_BWD);
+  const int prop_rows = op == OP_METRO_LEARNED ? 4 * (g->max_deg > 0 ? g->max_deg : 1) : 0;
+  p->prop_rows = prop_rows;
   const size_t budget = (size_t)di.smem_optin - 1024;  // room for static shared variables
   int G = 1;
   if (op == OP_ELOC_INCR) {
@@ -843,7 +1088,7 @@ gna_status simt_plan(const gna_graph* g, const Dims& m, int op, int64_t B, Plan*
     Carve cv = carve(m, G, sizeof(T), 1, rel);
     part_smem = cv.total <= budget || carve(m, G, sizeof(T), 1, 0).total <= budget;
   }
-  Carve in = carve(m, G, sizeof(T), part_smem, rel);
+  Carve in = carve(m, G, sizeof(T), part_smem, rel, prop_rows);
   p->G = G;
   p->region_elems = rel;
   p->partial_in_smem = part_smem;
@@ -851,7 +1096,7 @@ gna_status simt_plan(const gna_graph* g, const Dims& m, int op, int64_t B, Plan*
     p->region_in_smem = 1;
     p->smem = (int)in.total;
   } else {
-    Carve out = carve(m, G, sizeof(T), part_smem, 0);
+    Carve out = carve(m, G, sizeof(T), part_smem, 0, prop_rows);
     if (out.total > budget) return GNA_ERR_UNSUPPORTED;
     p->region_in_smem = 0;
     p->smem = (int)out.total;
@@ -881,7 +1126,8 @@ gna_status simt_launch(const SimtCall& sc, void* ws, size_t ws_bytes, cudaStream
     return GNA_OK;
   }
   Plan p;
-  gna_status st = simt_plan<T>(sc.g, sc.m, sc.op, sc.B, &p);
+  const int plan_op = (sc.op == OP_METRO && sc.prop) ? (int)OP_METRO_LEARNED : sc.op;
+  gna_status st = simt_plan<T>(sc.g, sc.m, plan_op, sc.B, &p);
   if (st != GNA_OK) return st;
   if (ws_bytes < p.ws_bytes || (p.ws_bytes > 0 && ws == nullptr)) return GNA_ERR_WORKSPACE;
   SimtArgs<T> a;
@@ -909,6 +1155,9 @@ gna_status simt_launch(const SimtCall& sc, void* ws, size_t ws_bytes, cudaStream
   a.region_elems = p.region_elems;
   a.region_in_smem = p.region_in_smem;
   a.partial_in_smem = p.partial_in_smem;
+  a.prop = sc.op == OP_METRO ? sc.prop : nullptr;
+  a.prop_eps = sc.prop_eps;
+  a.prop_rows = p.prop_rows;
   unsigned char* w = (unsigned char*)ws;
   a.gregion = nullptr;
   if (!p.region_in_smem) {
@@ -1017,6 +1266,9 @@ static gna_status backward_static_launch(const SimtCall& sc, cudaStream_t stream
   a.region_elems = p.region_elems;
   a.region_in_smem = p.region_in_smem;
   a.partial_in_smem = p.partial_in_smem;
+  a.prop = nullptr;
+  a.prop_eps = 0.0;
+  a.prop_rows = 0;
   // Every block zeroes its own partial before accumulating and the reduction reads
   // only what this launch wrote, so nothing left by an earlier call is used.
   unsigned char* w = (unsigned char*)base;

@@ -8,8 +8,10 @@
 // (r/8)*SBO + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes, SBO = 32F.  B = W^T (F x 2F) uses the
 // same form.  One elected thread issues 2F/16 MMAs of M=128, N=F, K=16 per tile into a
 // TMEM accumulator (column offset tile*F) and commits them to an mbarrier; all warps
-// then read the accumulator with tcgen05.ld (warp w sees lanes 32*(w%4)..+31, warp
-// group w/4 takes half of the columns), add the bias, apply tanh and store the new rows.
+// then read the accumulator with tcgen05.ld (warp w sees lanes 32*(w%4)..+31; the
+// 8-column chunks are spread over the four warp groups), add the bias, apply tanh and
+// store the new rows.  Feature rows are stored with padded strides (F + 8 BF16, F + 4
+// FP32) so that lanes reading rows of different sites do not share banks.
 //
 // Storage: cached layers H^0..H^{L-1} are BF16, as the GEMM consumes them; the FP32
 // pre-activations Y^1..Y^L are cached for the incremental step.
@@ -36,7 +38,8 @@ namespace gna {
 
 static __device__ int s_tc_status;
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
+constexpr int kTcGroups = kTcThreads / 128;  // warp groups (4 warps each)
 constexpr int kTmemCols = 128;
 constexpr uint32_t kWaitLimit = 1u << 26;            // try_wait iterations
 constexpr uint64_t kWaitNs = 2000000000ull;          // and at most 2 s of wall time
@@ -211,15 +214,16 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     r += bytes;
     return x;
   };
-  t->rcache16 = rtake((uint64_t)L * N * F * 2);
-  t->rY = rtake((uint64_t)L * N * F * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
+  const uint64_t ldh = F + 8, ldy = F + 4;  // padded row strides (BF16 rows, FP32 rows)
+  t->rcache16 = rtake((uint64_t)L * N * ldh * 2);
+  t->rY = rtake((uint64_t)L * N * ldy * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
   uint64_t n16 = 0;
   for (int l = 0; l < L; ++l) {
     t->new16_off[l] = n16;
-    n16 += (uint64_t)G * maxball[l] * F * 2;
+    n16 += (uint64_t)G * maxball[l] * ldh * 2;
   }
   t->rnew16 = rtake(n16);
-  t->rpart = rtake((uint64_t)2 * t->T * 128 * 2 * 4);  // [warp group][row][Re, Im] partial Delta
+  t->rpart = rtake((uint64_t)kTcGroups * t->T * 128 * 2 * 4);  // [warp group][row][Re, Im] partial Delta
   t->region_bytes = (r + 255) / 256 * 256;
   if (region_in_smem) {
     t->oregion = take(t->region_bytes, 16);
@@ -236,6 +240,7 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
 struct TcCtx {
   const TcArgs* a;
   int N, F, L, E, T, G;
+  int ldh, ldy;  // row strides: BF16 feature rows, FP32 pre-activation rows
   unsigned char* smem;
   __nv_bfloat16* Wt;
   unsigned char* A;
@@ -258,15 +263,15 @@ __device__ __forceinline__ unsigned char* a_row_chunk(const TcCtx& c, int q, int
 }
 
 __device__ __forceinline__ const __nv_bfloat16* cache16(const TcCtx& c, int l) {
-  return (const __nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.F;
+  return (const __nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.ldh;
 }
 __device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
-  return (__nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.F;
+  return (__nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.ldh;
 }
 // FP32 pre-activation Y^l (l = 1..L) of every site; for the forward-only call the last
 // slot holds H^L instead.
 __device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
-  return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.F;
+  return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.ldy;
 }
 __device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, int l) {
   return (__nv_bfloat16*)(c.region + c.a->lay.rnew16 + c.a->lay.new16_off[l]);
@@ -323,19 +328,19 @@ __device__ bool run_mmas(TcCtx& c, int nt) {
 __device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool keep_y) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q4 = warp & 3, wg = warp >> 2;
-  const int F = c.F, half = F / 2, L = c.L;
-  __nv_bfloat16* h16 = l < L ? cache16w(c, l) + (size_t)r0 * F : nullptr;
-  float* y32 = cacheY(c, l) + (size_t)r0 * F;
+  const int F = c.F, L = c.L, ldh = c.ldh, ldy = c.ldy;
+  __nv_bfloat16* h16 = l < L ? cache16w(c, l) + (size_t)r0 * ldh : nullptr;
+  float* y32 = cacheY(c, l) + (size_t)r0 * ldy;
   for (int t = 0; t < nt; ++t) {
     const int q = t * 128 + q4 * 32 + lane;
-    for (int j = 0; j < half / 8; ++j) {
-      const int col = wg * half + j * 8;
+    for (int ch = wg; ch < F / 8; ch += kTcGroups) {
+      const int col = ch * 8;
       float v[8];
       tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), v);
       if (q < R) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] += c.bias[col + i];
-        float4* yo = reinterpret_cast<float4*>(y32 + (size_t)q * F + col);
+        float4* yo = reinterpret_cast<float4*>(y32 + (size_t)q * ldy + col);
         if (l < L) {
           if (keep_y) {
             yo[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -346,7 +351,7 @@ __device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool 
           w.y = pack_bf16(tanh_fast(v[2]), tanh_fast(v[3]));
           w.z = pack_bf16(tanh_fast(v[4]), tanh_fast(v[5]));
           w.w = pack_bf16(tanh_fast(v[6]), tanh_fast(v[7]));
-          *reinterpret_cast<uint4*>(h16 + (size_t)q * F + col) = w;
+          *reinterpret_cast<uint4*>(h16 + (size_t)q * ldh + col) = w;
         } else if (keep_y) {
           yo[0] = make_float4(v[0], v[1], v[2], v[3]);
           yo[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -363,40 +368,40 @@ __device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool 
 
 // Forward of the configuration in c.spin: fills the cache (layers 0..L-1 BF16, L FP32).
 __device__ bool tc_forward(TcCtx& c) {
-  const int N = c.N, F = c.F, L = c.L;
+  const int N = c.N, F = c.F, L = c.L, ldh = c.ldh;
   const DevGraph& g = c.a->g;
   // layer 0: embedding rows
   __nv_bfloat16* c0 = cache16w(c, 0);
   for (int i = threadIdx.x; i < N * F; i += blockDim.x)
-    c0[i] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
+    c0[(size_t)(i / F) * ldh + i % F] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
   __syncthreads();
-  const int C8 = (2 * F) / 8, F8 = F / 8;
+  const int F8 = F / 8;
   const int rows_per_pass = c.T * 128;
   for (int l = 1; l <= L; ++l) {
     const __nv_bfloat16* hp = cache16(c, l - 1);
     for (int r0 = 0; r0 < N; r0 += rows_per_pass) {
       const int R = min(rows_per_pass, N - r0);
       const int nt = (R + 127) / 128;
-      const int items = ((R + 7) / 8) * 8 * C8;
-      for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-        const int q8 = idx & 7, ch = (idx >> 3) % C8, qb = (idx >> 3) / C8;
-        const int q = qb * 8 + q8;
-        if (q >= R) continue;
-        const int v = r0 + q;
-        uint4 outw;
-        if (ch < F8) {
-          float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          const int k1 = __ldg(g.row_ptr + v + 1);
-          for (int k = __ldg(g.row_ptr + v); k < k1; ++k)
-            fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * F + ch * 8);
-          outw.x = pack_bf16(acc[0], acc[1]);
-          outw.y = pack_bf16(acc[2], acc[3]);
-          outw.z = pack_bf16(acc[4], acc[5]);
-          outw.w = pack_bf16(acc[6], acc[7]);
+      // one thread per (row, half): half 0 writes the message chunks, half 1 the self chunks
+      for (int idx = threadIdx.x; idx < 2 * R; idx += blockDim.x) {
+        const int q = idx >> 1, v = r0 + q;
+        if ((idx & 1) == 0) {
+          const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+          for (int ch = 0; ch < F8; ++ch) {
+            float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
+            uint4 w;
+            w.x = pack_bf16(acc[0], acc[1]);
+            w.y = pack_bf16(acc[2], acc[3]);
+            w.z = pack_bf16(acc[4], acc[5]);
+            w.w = pack_bf16(acc[6], acc[7]);
+            *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = w;
+          }
         } else {
-          outw = *reinterpret_cast<const uint4*>(hp + (size_t)v * F + (ch - F8) * 8);
+          for (int ch = 0; ch < F8; ++ch)
+            *reinterpret_cast<uint4*>(a_row_chunk(c, q, F8 + ch)) =
+                *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
         }
-        *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
       }
       if (!run_mmas(c, nt)) return false;
       epilogue_fwd(c, nt, R, r0, l, c.a->op == TC_ELOC);
@@ -414,7 +419,7 @@ __device__ void tc_readout(const TcCtx& c, double out[2]) {
   const int f = threadIdx.x % F, part = threadIdx.x / F;
   if (part < parts) {
     float acc = 0.f;
-    for (int v = part; v < N; v += parts) acc += HL[(size_t)v * F + f];
+    for (int v = part; v < N; v += parts) acc += HL[(size_t)v * c.ldy + f];
     red[part * F + f] = acc;
   }
   __syncthreads();
@@ -448,45 +453,47 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
 
 // dX rows of a bond group at layer l, gathered into the A tiles:
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
+// One thread per (row, half): half 0 writes the message chunks, half 1 the self chunks.
 __device__ void gather_delta(const TcCtx& c, int l, const int* slot_e, int nb, const int* soff) {
   const DevGraph& g = c.a->g;
-  const int F = c.F, G = c.G;
-  const int C8 = (2 * F) / 8, F8 = F / 8;
+  const int F = c.F, G = c.G, ldh = c.ldh;
+  const int F8 = F / 8;
   const int* offp = soff + (l - 1) * (G + 1);
   const int* offl = soff + l * (G + 1);
   const int R = offl[nb];
   const __nv_bfloat16* dp = new16(c, l - 1);
-  const int items = ((R + 7) / 8) * 8 * C8;
-  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
-    const int q8 = idx & 7, ch = (idx >> 3) % C8, qb = (idx >> 3) / C8;
-    const int q = qb * 8 + q8;
-    if (q >= R) continue;
+  for (int idx = threadIdx.x; idx < 2 * R; idx += blockDim.x) {
+    const int q = idx >> 1;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
     const int e = slot_e[k];
     const int bo = __ldg(g.ball_off + e);
     const int sprev = offp[k + 1] - offp[k];
-    const __nv_bfloat16* drow = dp + (size_t)offp[k] * F;
-    uint4 outw;
-    if (ch < F8) {
-      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh;
+    if ((idx & 1) == 0) {
       const int v = __ldg(g.ball_vert + bo + r);
       const int nb0 = __ldg(g.row_nbr + bo + r);
       const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
-      for (int kk = k0; kk < k1; ++kk) {
-        const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
-        if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * F + ch * 8);
+      for (int ch = 0; ch < F8; ++ch) {
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int kk = k0; kk < k1; ++kk) {
+          const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
+          if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * ldh + ch * 8);
+        }
+        uint4 w;
+        w.x = pack_bf16(acc[0], acc[1]);
+        w.y = pack_bf16(acc[2], acc[3]);
+        w.z = pack_bf16(acc[4], acc[5]);
+        w.w = pack_bf16(acc[6], acc[7]);
+        *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = w;
       }
-      outw.x = pack_bf16(acc[0], acc[1]);
-      outw.y = pack_bf16(acc[2], acc[3]);
-      outw.z = pack_bf16(acc[4], acc[5]);
-      outw.w = pack_bf16(acc[6], acc[7]);
-    } else if (r < sprev) {
-      outw = *reinterpret_cast<const uint4*>(drow + (size_t)r * F + (ch - F8) * 8);
     } else {
-      outw = make_uint4(0u, 0u, 0u, 0u);
+      for (int ch = 0; ch < F8; ++ch) {
+        const uint4 w = r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh + ch * 8)
+                                  : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(a_row_chunk(c, q, F8 + ch)) = w;
+      }
     }
-    *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = outw;
   }
 }
 
@@ -497,7 +504,7 @@ __device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e,
   const DevGraph& g = c.a->g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q4 = warp & 3, wg = warp >> 2;
-  const int F = c.F, half = F / 2, L = c.L, G = c.G;
+  const int F = c.F, L = c.L, G = c.G, ldh = c.ldh, ldy = c.ldy;
   const int* offl = soff + l * (G + 1);
   const int R = offl[nb];
   __nv_bfloat16* dout = l < L ? new16(c, l) : nullptr;
@@ -511,13 +518,13 @@ __device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e,
       v = __ldg(g.ball_vert + __ldg(g.ball_off + slot_e[k]) + (q - offl[k]));
     }
     float pre = 0.f, pim = 0.f;
-    for (int j = 0; j < half / 8; ++j) {
-      const int col = wg * half + j * 8;
+    for (int ch = wg; ch < F / 8; ch += kTcGroups) {
+      const int col = ch * 8;
       float dy[8];
       tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
       if (q < R) {
-        const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * F + col);
-        const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * F + col + 4);
+        const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col);
+        const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
         const float y[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         float d[8];
 #pragma unroll
@@ -539,7 +546,7 @@ __device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e,
           w.y = pack_bf16(d[2], d[3]);
           w.z = pack_bf16(d[4], d[5]);
           w.w = pack_bf16(d[6], d[7]);
-          *reinterpret_cast<uint4*>(dout + (size_t)q * F + col) = w;
+          *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
         } else {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -580,7 +587,7 @@ __device__ bool tc_group(TcCtx& c, const int* slot_e, int nb, int* soff) {
     const int e = slot_e[k];
     const int self = __ldg(g.edges + 2 * e + r), other = __ldg(g.edges + 2 * e + (1 - r));
     const float dv = c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f] - c.emb[(c.spin[self] > 0 ? 0 : 1) * F + f];
-    d0[(size_t)(soff[k] + r) * F + f] = __float2bfloat16_rn(dv);
+    d0[(size_t)(soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
   }
   __syncthreads();
   for (int l = 1; l <= L; ++l) {
@@ -597,8 +604,10 @@ __device__ bool tc_group(TcCtx& c, const int* slot_e, int nb, int* soff) {
   for (int k = warp; k < nb; k += nwarps) {
     float dre = 0.f, dim = 0.f;
     for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
-      dre += part[q * 2] + part[(wgs + q) * 2];
-      dim += part[q * 2 + 1] + part[(wgs + q) * 2 + 1];
+      for (int w = 0; w < min(kTcGroups, F / 8); ++w) {
+        dre += part[(w * wgs + q) * 2];
+        dim += part[(w * wgs + q) * 2 + 1];
+      }
     }
     dre = warp_sum_t(dre);
     dim = warp_sum_t(dim);
@@ -623,6 +632,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   c.E = a.m.E;
   c.T = a.lay.T;
   c.G = a.lay.G;
+  c.ldh = a.m.F + 8;
+  c.ldy = a.m.F + 4;
   c.smem = smem;
   c.Wt = (__nv_bfloat16*)(smem + a.lay.oWt);
   c.A = smem + a.lay.oA;

@@ -27,14 +27,16 @@ GNA_WARN_DEGENERATE_WEIGHTS = 1
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 ACT_TANH = 0
 ELOC_FULL, ELOC_INCREMENTAL = 0, 1
-OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIGHTS, OP_ISGO_GRAD = range(7)
+OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIGHTS, OP_ISGO_GRAD, \
+    OP_METROPOLIS_LEARNED = range(8)
 
 EXPORTED = [
     "gna_version", "gna_status_string", "gna_graph_create", "gna_graph_destroy", "gna_graph_info",
     "gna_ball_sizes_host", "gna_model_desc_init", "gna_num_params", "gna_workspace_size", "gna_forward",
     "gna_local_energy", "gna_metropolis_sweep", "gna_backward", "gna_backward_static", "gna_isgo_weights_workspace",
     "gna_isgo_weights", "isgo_grad",
-    "gna_sgd_update", "gna_philox4x64_10", "gna_device_status",
+    "gna_sgd_update", "gna_philox4x64_10", "gna_device_status", "gna_proposal_num_params",
+    "gna_proposal_workspace_size", "gna_proposal_logits", "gna_proposal_grad", "gna_proposal_adam",
 ]
 
 
@@ -82,7 +84,12 @@ def lib():
             "gna_forward": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, sz, vp]),
             "gna_local_energy": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, i32, vp, vp, vp, sz, vp]),
             "gna_metropolis_sweep": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, i32, i32, u64, u64,
-                                           vp, vp, vp, vp, vp, sz, vp]),
+                                           vp, dbl, vp, vp, vp, vp, vp, sz, vp]),
+            "gna_proposal_num_params": (i32, []),
+            "gna_proposal_workspace_size": (i32, [vp, i64, ctypes.POINTER(sz)]),
+            "gna_proposal_logits": (i32, [vp, vp, i64, vp, vp, vp]),
+            "gna_proposal_grad": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]),
+            "gna_proposal_adam": (i32, [vp, vp, vp, vp, i32, dbl, vp]),
             "gna_backward": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]),
             "gna_backward_static": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, vp]),
             "gna_isgo_weights_workspace": (i32, [i64, ctypes.POINTER(sz)]),
@@ -266,8 +273,13 @@ def local_energy(graph: Graph, model: Model, theta, spins, mode: int = ELOC_INCR
 
 
 def metropolis_sweep(graph: Graph, model: Model, theta, chain_spins, n_sweeps: int, record_every: int, seed: int,
-                     step0: int, trace: bool = False, n_accepted=None, records: bool = True):
-    """Advance the chains in place; returns (samples [R][C][N] int8, logpsi [R][C][2], n_accepted [C], trace)."""
+                     step0: int, trace: bool = False, n_accepted=None, records: bool = True, proposal=None,
+                     eps: float = 0.1):
+    """Advance the chains in place; returns (samples [R][C][N] int8, logpsi [R][C][2], n_accepted [C], trace).
+
+    proposal: float32 CUDA tensor of the proposal network's parameters (learned moves
+    mixed with plain ones with probability eps) or None (plain moves).  trace rows are
+    (bond or -1, accepted, value, kind)."""
     torch = _check_theta(model, theta)
     _check_spins(graph, chain_spins)
     C = chain_spins.shape[0]
@@ -276,13 +288,58 @@ def metropolis_sweep(graph: Graph, model: Model, theta, chain_spins, n_sweeps: i
     samples = torch.empty((R, C, graph.n_sites), dtype=torch.int8, device=dev) if R else None
     lpo = torch.empty((R, C, 2), dtype=torch.float64, device=dev) if R else None
     acc = n_accepted if n_accepted is not None else torch.zeros(C, dtype=torch.int32, device=dev)
-    tr = torch.empty((C, n_sweeps * graph.n_sites, 3), dtype=torch.float64, device=dev) if trace else None
-    w, wn = _ws_for(graph, model, OP_METROPOLIS, C)
+    tr = torch.empty((C, n_sweeps * graph.n_sites, 4), dtype=torch.float64, device=dev) if trace else None
+    op = OP_METROPOLIS_LEARNED if proposal is not None else OP_METROPOLIS
+    w, wn = _ws_for(graph, model, op, C)
     _check(lib().gna_metropolis_sweep(graph.handle, ctypes.byref(model.desc), theta.data_ptr(),
                                       chain_spins.data_ptr(), C, n_sweeps, record_every if R else 0, seed, step0,
-                                      _ptr(samples), _ptr(lpo), acc.data_ptr(), _ptr(tr), w, wn, _stream()),
+                                      _ptr(proposal), float(eps), _ptr(samples), _ptr(lpo), acc.data_ptr(), _ptr(tr),
+                                      w, wn, _stream()),
            "gna_metropolis_sweep")
     return samples, lpo, acc, tr
+
+
+# ---------------------------------------------------------------------------------
+# learned proposal
+# ---------------------------------------------------------------------------------
+
+def proposal_num_params() -> int:
+    return int(lib().gna_proposal_num_params())
+
+
+def proposal_logits(graph: Graph, spins, params):
+    """float32 [B][E][2] logits (NaN on parallel bonds)."""
+    import torch
+
+    _check_spins(graph, spins)
+    B = spins.shape[0]
+    out = torch.empty((B, graph.n_edges, 2), dtype=torch.float32, device=spins.device)
+    _check(lib().gna_proposal_logits(graph.handle, spins.data_ptr(), B, params.data_ptr(), out.data_ptr(), _stream()),
+           "gna_proposal_logits")
+    return out
+
+
+def proposal_grad(graph: Graph, spins, dlogpsi_bonds, params):
+    """(grad float64 [P], loss float64 [1]) of the proposal network's training loss."""
+    import torch
+
+    _check_spins(graph, spins)
+    B = spins.shape[0]
+    grad = torch.empty(proposal_num_params(), dtype=torch.float64, device=spins.device)
+    loss = torch.empty(1, dtype=torch.float64, device=spins.device)
+    n = sz(0)
+    _check(lib().gna_proposal_workspace_size(graph.handle, B, ctypes.byref(n)), "gna_proposal_workspace_size")
+    w = workspace(int(n.value))
+    _check(lib().gna_proposal_grad(graph.handle, spins.data_ptr(), dlogpsi_bonds.contiguous().data_ptr(), B,
+                                   params.data_ptr(), grad.data_ptr(), loss.data_ptr(), w.data_ptr(), w.numel(),
+                                   _stream()), "gna_proposal_grad")
+    return grad, loss
+
+
+def proposal_adam(params, m, v, grad, t: int, lr: float):
+    _check(lib().gna_proposal_adam(params.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), int(t), float(lr),
+                                   _stream()), "gna_proposal_adam")
+    return params
 
 
 def backward(graph: Graph, model: Model, theta, spins, cot, out=None):

@@ -1,0 +1,141 @@
+"""GPU parity of the learned exchange proposal against the FP64 oracle (oracle/proposal.py):
+network logits and training gradient (FP32 kernels, 1e-4 relative), the Adam step, and
+the learned-move Metropolis-Hastings chains (FP64 path: identical moves, decisions and
+states, log acceptance ratios within 1e-9)."""
+import numpy as np
+import pytest
+
+from oracle import gcn, heisenberg as hz, proposal as P
+from paper_2011_12453_gb300 import build as B, gna, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    B.build()
+    t.cuda.set_device(0)
+    return t
+
+
+def _params(torch, seed, scale=0.5):
+    p32 = torch.tensor(W.random_proposal_params(seed, scale), dtype=torch.float32, device="cuda")
+    return p32, p32.double().cpu().numpy()  # the oracle runs on the float32-rounded values
+
+
+@pytest.mark.parametrize("gname", ["kagome6", "er30"])
+def test_logits_parity(torch, gname):
+    g = W.kagome(6) if gname == "kagome6" else W.erdos_renyi(30, 0.15, seed=3, J_range=(0.5, 1.5))
+    graph = gna.Graph.from_workload(g, 1)
+    p32, pnp = _params(torch, 1)
+    s = W.random_spins(g.n_sites, 5, seed=2)
+    got = gna.proposal_logits(graph, torch.tensor(s, device="cuda"), p32).cpu().numpy()
+    top = P.Topology(g.n_sites, g.edges, g.J)
+    for b in range(5):
+        for e, (i, j) in enumerate(g.edges.tolist()):
+            if s[b, i] == s[b, j]:
+                assert np.isnan(got[b, e]).all()
+                continue
+            want = P.mlp(pnp, np.stack([P.features(top, s[b], i, j), P.features(top, s[b], j, i)]))[0]
+            np.testing.assert_allclose(got[b, e], want, rtol=1e-4, atol=1e-5)
+
+
+def test_gradient_parity(torch):
+    g = W.kagome(2)
+    graph = gna.Graph.from_workload(g, 1)
+    p32, pnp = _params(torch, 2)
+    s = W.random_spins(g.n_sites, 37, seed=4)
+    dl = np.random.default_rng(5).normal(scale=0.5, size=(37, g.n_edges)).astype(np.float32)
+    grad, loss = gna.proposal_grad(graph, torch.tensor(s, device="cuda"), torch.tensor(dl, device="cuda"), p32)
+    top = P.Topology(g.n_sites, g.edges, g.J)
+    phi, tgt = P.training_rows(top, s, dl.astype(np.float64))
+    want_loss, want_grad = P.loss_and_grad(pnp, phi, tgt)
+    assert abs(loss.item() - want_loss) <= 1e-4 * abs(want_loss)
+    np.testing.assert_allclose(grad.cpu().numpy(), want_grad, rtol=0, atol=1e-4 * np.abs(want_grad).max())
+
+
+def test_adam_parity(torch):
+    p32, pnp = _params(torch, 3)
+    n = p32.numel()
+    rng = np.random.default_rng(6)
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    mo, vo, po = np.zeros(n), np.zeros(n), pnp.copy()
+    for t in (1, 2, 3):
+        g = rng.normal(size=n)
+        gna.proposal_adam(p32, m, v, torch.tensor(g, device="cuda"), t, 1e-3)
+        po, mo, vo = P.adam_step(po, g, mo, vo, t, 1e-3)
+    np.testing.assert_allclose(p32.double().cpu().numpy(), po, rtol=0, atol=1e-6)
+
+
+def test_learned_metropolis_fp64_matches_oracle(torch):
+    g = W.kagome(2)
+    F, L = 8, 2
+    th = W.random_theta(F, L, seed=1, scale=0.8)
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_FP64)
+    theta = torch.tensor(th, device="cuda")
+    p32, pnp = _params(torch, 4, scale=1.0)
+    Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
+    C, sweeps, seed, step0, eps = 6, 2, 77, 5, 0.25
+    s0 = W.random_spins(g.n_sites, C, seed=8)
+    ch = torch.tensor(s0, device="cuda")
+    _, _, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, sweeps, 0, seed, step0, trace=True, proposal=p32,
+                                         eps=eps)
+    top = P.Topology(g.n_sites, g.edges, g.J)
+    s_o, acc_o, tr_o = P.run_chains(lambda x: gcn.logpsi_complex(th, F, L, Ah, np.atleast_2d(x)), top, pnp, s0, seed,
+                                    step0, sweeps, eps)
+    tr = tr.cpu().numpy()
+    for c in range(C):
+        for k in range(tr.shape[1]):
+            kind, i, j, ok, lr = tr_o[c, k]
+            assert tr[c, k, 3] == kind, (c, k)
+            e = top.bond[(int(i), int(j))] if j >= 0 else -1
+            assert tr[c, k, 0] == e, (c, k)
+            assert tr[c, k, 1] == ok, (c, k)
+            if np.isnan(lr):
+                assert np.isnan(tr[c, k, 2])
+            else:
+                assert abs(tr[c, k, 2] - lr) < 1e-9, (c, k, tr[c, k, 2], lr)
+    assert np.array_equal(ch.cpu().numpy(), s_o)
+    assert np.array_equal(acc.cpu().numpy(), acc_o)
+
+
+def test_learned_metropolis_conserves_sz_and_stays_finite(torch):
+    g = W.erdos_renyi(40, 0.1, seed=7, J_range=(0.5, 1.5))
+    F, L = 16, 3
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_FP32)
+    theta = torch.tensor(W.random_theta(F, L, seed=2, scale=0.3), dtype=torch.float32, device="cuda")
+    p32, _ = _params(torch, 5)
+    ch = torch.tensor(W.random_spins(g.n_sites, 64, seed=3), device="cuda")
+    samples, lp, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, 3, 1, 5, 0, trace=True, proposal=p32,
+                                                eps=0.1)
+    x = samples.cpu().numpy()
+    assert np.all((x > 0).sum(-1) == g.n_sites // 2)
+    t = tr.cpu().numpy()
+    assert set(np.unique(t[:, :, 3])) <= {1.0, 2.0}
+    assert (t[:, :, 3] == 2).mean() > 0.8  # eps = 0.1 of the steps are plain
+    assert acc.cpu().numpy().sum() == t[:, :, 1].sum() > 0
+    assert np.all(np.isfinite(lp.cpu().numpy()))
+
+
+def test_training_reduces_loss(torch):
+    g = W.kagome(6)
+    F, L = 32, 4
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_FP32)
+    theta = torch.tensor(W.random_theta(F, L, seed=0, scale=0.3), dtype=torch.float32, device="cuda")
+    s = torch.tensor(W.random_spins(g.n_sites, 512, seed=1), device="cuda")
+    _, dl = gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, bonds=True)
+    p32, _ = _params(torch, 6)
+    m = torch.zeros_like(p32)
+    v = torch.zeros_like(p32)
+    losses = []
+    for t in range(1, 61):
+        grad, loss = gna.proposal_grad(graph, s, dl, p32)
+        losses.append(loss.item())
+        gna.proposal_adam(p32, m, v, grad, t, 3e-3)
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])

@@ -1,0 +1,436 @@
+// Metropolis pair-exchange sweeps with one warp per chain (plain moves).
+//
+// Sampling P ~ |Psi|^2 (scaling section of arXiv:2011.12453) needs, per proposed exchange
+// of an antiparallel pair (i, j), the ratio Psi(s')/Psi(s).  It is computed by propagating
+// the change of the node features through the GCN layers of Eq. (gcn), restricted to the
+// nested neighbourhoods ball_l(e) of the bond:
+//   dH^0 = rows i, j of the embedding difference;
+//   dY^l = [A_hat dH^{l-1} ; dH^{l-1}] W   (the bias cancels; zero outside ball_l),
+//   dH^l = tanh(Y^l + dY^l) - tanh(Y^l) = t (1 - H^2)/(1 + H t),  t = tanh(dY^l),
+//   Delta log Psi = w_r[:F] . sum_v dH^L_v.
+// The chain keeps the pre-activations Y^1..Y^L of its current state (in a per-warp slice of
+// the workspace, L2-resident); an accepted move adds dY^l to the rows of ball_l.
+//
+// A warp owns a chain at a time: no block barriers, only warp-synchronous steps, so the
+// latency of one chain's step is hidden behind the other warps' chains.  Lanes own
+// feature columns (f = lane, lane + 32).  The Philox words of 32 consecutive steps are
+// drawn at once, one step per lane, and broadcast by shuffles.
+#include <climits>
+#include <cmath>
+
+#include "common.cuh"
+#include "metro.cuh"
+
+namespace gna {
+
+constexpr int kMetroMaxWarps = 8;  // chains per CTA at most (fewer when shared memory is short)
+
+template <typename T>
+struct MetroArgs {
+  DevGraph g;
+  Dims m;
+  int maxball[kMaxL + 1];
+  int off_dh[kMaxL + 1];  // per-warp smem element offsets of dH^l rows (l < L)
+  int off_dy[kMaxL + 1];  // ... and of dY^l rows (l = 1..L)
+  int warp_elems;         // elements of T per warp in shared memory
+  int nwarps;             // warps (chains in flight) per CTA
+  const T* theta;
+  int8_t* chain_spins;
+  int64_t C;
+  int32_t n_sweeps, record_every;
+  uint64_t seed, step0;
+  int8_t* samples_out;
+  double* logpsi_out;
+  int32_t* n_acc;
+  double* trace;
+  T* gws;          // per warp slot: Y^1..Y^L [L][N][F] then two H scratch rows [2][N][F]
+  size_t ws_elems; // elements per warp slot
+};
+
+__device__ __forceinline__ double m_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float m_tanh(float x) { return tanhf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// dH = tanh(y + dy) - tanh(y), in the stable form t (1 - H^2)/(1 + H t) built from
+// e = exp(-2|y|); falls back to the direct difference when 1 + H t is small (a unit
+// swinging across saturation, where dH is O(1) and the difference has no cancellation).
+template <typename T>
+__device__ __forceinline__ T dtanh(T y, T dy) {
+  const T e = m_exp((T)-2 * fabs(y));
+  const T t = m_tanh(dy);
+  const T sg = y < (T)0 ? (T)-1 : (T)1;
+  const T ope = (T)1 + e;
+  const T den = ope * (ope + sg * ((T)1 - e) * t);
+  return den > (T)1e-3 ? m_div((T)4 * e * t, den) : m_tanh(y + dy) - m_tanh(y);
+}
+
+template <typename T>
+__device__ inline bool m_accept(uint64_t r1, T dre);
+template <>
+__device__ inline bool m_accept<double>(uint64_t r1, double dre) {
+  return (double)(r1 >> 11) * 0x1.0p-53 < exp(2.0 * dre);
+}
+template <>
+__device__ inline bool m_accept<float>(uint64_t r1, float dre) {
+  return (float)(r1 >> 40) * 0x1.0p-24f < expf(2.0f * dre);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevGraph& g = a.g;
+  const Dims& m = a.m;
+  const int N = m.N, F = m.F, L = m.L, E = m.E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ldw = F + 1;
+  // block-shared parameters
+  T* sW = (T*)smem;                  // [2F][F+1]
+  T* sb = sW + 2 * F * ldw;          // [F]
+  T* semb = sb + F;                  // [2][F]
+  T* swr = semb + 2 * F;             // [(F+2)][2]
+  T* sbr = swr + (F + 2) * 2;        // [2]
+  T* wbase = sbr + 2;
+  const size_t param_elems = (size_t)2 * F * ldw + F + 2 * F + (F + 2) * 2 + 2;
+  const size_t param_pad = (param_elems + 3) / 4 * 4;
+  wbase = (T*)smem + param_pad;
+  T* wsm = wbase + (size_t)warp * a.warp_elems;               // this warp's dH / dY rows
+  int8_t* spin = (int8_t*)(wbase + (size_t)a.nwarps * a.warp_elems) + (size_t)warp * ((N + 15) / 16 * 16);
+  const T* th = a.theta;
+  for (int i = threadIdx.x; i < 2 * F * F; i += blockDim.x) sW[(i / F) * ldw + i % F] = th[m.oW + i];
+  for (int i = threadIdx.x; i < F; i += blockDim.x) sb[i] = th[m.ob + i];
+  for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) semb[i] = m_tanh(th[m.oWe + i] + th[m.obe + i % F]);
+  for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) swr[i] = th[m.owr + i];
+  if (threadIdx.x < 2) sbr[threadIdx.x] = th[m.obr + threadIdx.x];
+  __syncthreads();
+
+  const int64_t gwarp = (int64_t)blockIdx.x * a.nwarps + warp;
+  const int64_t nwarps = (int64_t)gridDim.x * a.nwarps;
+  T* Ybase = a.gws + (size_t)gwarp * a.ws_elems;  // Y^l at Ybase + (l-1)*N*F
+  T* Hs0 = Ybase + (size_t)L * N * F;
+  T* Hs1 = Hs0 + (size_t)N * F;
+  const int f0 = lane, f1 = lane + 32;
+  const bool has0 = f0 < F, has1 = f1 < F;
+  const int64_t n_steps = (int64_t)a.n_sweeps * N;
+  const int n_rec = a.record_every > 0 ? a.n_sweeps / a.record_every : 0;
+
+  for (int64_t ch = gwarp; ch < a.C; ch += nwarps) {
+    for (int v = lane; v < N; v += 32) spin[v] = a.chain_spins[ch * N + v];
+    __syncwarp();
+    // ---- forward: Y^1..Y^L of the chain's state (H scratch ping-pong) ----
+    for (int v = 0; v < N; ++v) {
+      const int c = spin[v] > 0 ? 0 : 1;
+      if (has0) Hs0[(size_t)v * F + f0] = semb[c * F + f0];
+      if (has1) Hs0[(size_t)v * F + f1] = semb[c * F + f1];
+    }
+    __syncwarp();
+    for (int l = 1; l <= L; ++l) {
+      const T* Hp = (l & 1) ? Hs0 : Hs1;
+      T* Hn = (l & 1) ? Hs1 : Hs0;
+      T* Y = Ybase + (size_t)(l - 1) * N * F;
+      for (int v = 0; v < N; ++v) {
+        T ag0 = 0, ag1 = 0;
+        const int k1 = __ldg(g.row_ptr + v + 1);
+        for (int k = __ldg(g.row_ptr + v); k < k1; ++k) {
+          const T w = (T)__ldg(g.wd + k);
+          const T* hu = Hp + (size_t)__ldg(g.col + k) * F;
+          if (has0) ag0 += w * hu[f0];
+          if (has1) ag1 += w * hu[f1];
+        }
+        const T sf0 = has0 ? Hp[(size_t)v * F + f0] : (T)0, sf1 = has1 ? Hp[(size_t)v * F + f1] : (T)0;
+        T y0 = has0 ? sb[f0] : (T)0, y1 = has1 ? sb[f1] : (T)0;
+        for (int kk = 0; kk < F; ++kk) {
+          const T av = __shfl_sync(0xffffffffu, kk < 32 ? ag0 : ag1, kk & 31);
+          const T sv = __shfl_sync(0xffffffffu, kk < 32 ? sf0 : sf1, kk & 31);
+          if (has0) y0 += av * sW[kk * ldw + f0] + sv * sW[(F + kk) * ldw + f0];
+          if (has1) y1 += av * sW[kk * ldw + f1] + sv * sW[(F + kk) * ldw + f1];
+        }
+        if (has0) {
+          Y[(size_t)v * F + f0] = y0;
+          Hn[(size_t)v * F + f0] = m_tanh(y0);
+        }
+        if (has1) {
+          Y[(size_t)v * F + f1] = y1;
+          Hn[(size_t)v * F + f1] = m_tanh(y1);
+        }
+      }
+      __syncwarp();
+    }
+    int accepts = 0;
+    uint64_t w0 = 0, w1 = 0;  // Philox words r0, r1 of step (k0 + lane)
+    for (int64_t k = 0; k < n_steps; ++k) {
+      if ((k & 31) == 0) {
+        const U64x4 w = philox4x64_10(a.seed, (uint64_t)ch, U64x4{a.step0 + (uint64_t)(k + lane), 0, 0, 0});
+        w0 = w.x;
+        w1 = w.y;
+      }
+      const uint64_t r0 = __shfl_sync(0xffffffffu, w0, (int)(k & 31));
+      const uint64_t r1 = __shfl_sync(0xffffffffu, w1, (int)(k & 31));
+      const int e = (int)__umul64hi(r0, (uint64_t)E);
+      const int i = __ldg(g.edges + 2 * e), j = __ldg(g.edges + 2 * e + 1);
+      double* tr = a.trace ? a.trace + ((size_t)ch * n_steps + k) * 4 : nullptr;
+      if (spin[i] == spin[j]) {
+        if (tr && lane == 0) {
+          tr[0] = (double)e;
+          tr[1] = 0.0;
+          tr[2] = __longlong_as_double(0x7ff8000000000000ll);
+          tr[3] = 1.0;
+        }
+      } else {
+        const int bo = __ldg(g.ball_off + e);
+        const int* bsz = g.ball_size + (size_t)e * (g.Lmax + 1);
+        // layer 0: dH^0 rows (i, j)
+        {
+          T* d0 = wsm + a.off_dh[0];
+          const int ci = spin[i] > 0 ? 0 : 1, cj = spin[j] > 0 ? 0 : 1;
+          if (has0) {
+            d0[f0] = semb[cj * F + f0] - semb[ci * F + f0];
+            d0[F + f0] = semb[ci * F + f0] - semb[cj * F + f0];
+          }
+          if (has1) {
+            d0[f1] = semb[cj * F + f1] - semb[ci * F + f1];
+            d0[F + f1] = semb[ci * F + f1] - semb[cj * F + f1];
+          }
+          __syncwarp();
+        }
+        T pre = 0, pim = 0;
+        for (int l = 1; l <= L; ++l) {
+          const int sprev = __ldg(bsz + l - 1), R = __ldg(bsz + l);
+          const T* dprev = wsm + a.off_dh[l - 1];
+          T* dcur = l < L ? wsm + a.off_dh[l] : nullptr;
+          T* dycur = wsm + a.off_dy[l];
+          const T* Y = Ybase + (size_t)(l - 1) * N * F;
+          for (int r = 0; r < R; ++r) {
+            const int v = __ldg(g.ball_vert + bo + r);
+            const int nb0 = __ldg(g.row_nbr + bo + r);
+            const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+            T ag0 = 0, ag1 = 0;
+            for (int kk = k0; kk < k1; ++kk) {
+              const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
+              if (p < sprev) {
+                const T w = (T)__ldg(g.wd + kk);
+                if (has0) ag0 += w * dprev[(size_t)p * F + f0];
+                if (has1) ag1 += w * dprev[(size_t)p * F + f1];
+              }
+            }
+            T sf0 = 0, sf1 = 0;
+            if (r < sprev) {
+              if (has0) sf0 = dprev[(size_t)r * F + f0];
+              if (has1) sf1 = dprev[(size_t)r * F + f1];
+            }
+            T y0 = 0, y1 = 0;
+            for (int q = 0; q < F; ++q) {
+              const T av = __shfl_sync(0xffffffffu, q < 32 ? ag0 : ag1, q & 31);
+              const T sv = __shfl_sync(0xffffffffu, q < 32 ? sf0 : sf1, q & 31);
+              if (has0) y0 += av * sW[q * ldw + f0] + sv * sW[(F + q) * ldw + f0];
+              if (has1) y1 += av * sW[q * ldw + f1] + sv * sW[(F + q) * ldw + f1];
+            }
+            if (has0) {
+              const T d = dtanh(Y[(size_t)v * F + f0], y0);
+              dycur[(size_t)r * F + f0] = y0;
+              if (l < L)
+                dcur[(size_t)r * F + f0] = d;
+              else {
+                pre += d * swr[2 * f0];
+                pim += d * swr[2 * f0 + 1];
+              }
+            }
+            if (has1) {
+              const T d = dtanh(Y[(size_t)v * F + f1], y1);
+              dycur[(size_t)r * F + f1] = y1;
+              if (l < L)
+                dcur[(size_t)r * F + f1] = d;
+              else {
+                pre += d * swr[2 * f1];
+                pim += d * swr[2 * f1 + 1];
+              }
+            }
+          }
+          __syncwarp();
+        }
+        const T dre = wsum(pre);
+        const T dim = wsum(pim);
+        (void)dim;
+        const bool acc = m_accept<T>(r1, dre);
+        if (tr && lane == 0) {
+          tr[0] = (double)e;
+          tr[1] = acc ? 1.0 : 0.0;
+          tr[2] = (double)dre;
+          tr[3] = 1.0;
+        }
+        if (acc) {
+          ++accepts;
+          for (int l = 1; l <= L; ++l) {
+            const int R = __ldg(bsz + l);
+            const T* dy = wsm + a.off_dy[l];
+            T* Y = Ybase + (size_t)(l - 1) * N * F;
+            for (int r = 0; r < R; ++r) {
+              const int v = __ldg(g.ball_vert + bo + r);
+              if (has0) Y[(size_t)v * F + f0] += dy[(size_t)r * F + f0];
+              if (has1) Y[(size_t)v * F + f1] += dy[(size_t)r * F + f1];
+            }
+          }
+          if (lane == 0) {
+            const int8_t t = spin[i];
+            spin[i] = spin[j];
+            spin[j] = t;
+          }
+        }
+        __syncwarp();
+      }
+      if ((k + 1) % N == 0 && a.record_every > 0) {
+        const int sweep = (int)((k + 1) / N);
+        if (sweep % a.record_every == 0) {
+          const int rec = sweep / a.record_every - 1;
+          if (rec < n_rec) {
+            if (a.samples_out)
+              for (int v = lane; v < N; v += 32) a.samples_out[((size_t)rec * a.C + ch) * N + v] = spin[v];
+            if (a.logpsi_out) {
+              // log Psi = sum_v [tanh(Y^L_v) ; onehot_v] . w_r + b_r
+              const T* YL = Ybase + (size_t)(L - 1) * N * F;
+              T z0 = 0, z1 = 0;
+              int up = 0;
+              for (int v = 0; v < N; ++v) {
+                if (has0) z0 += L > 0 ? m_tanh(YL[(size_t)v * F + f0]) : semb[(spin[v] > 0 ? 0 : 1) * F + f0];
+                if (has1) z1 += L > 0 ? m_tanh(YL[(size_t)v * F + f1]) : semb[(spin[v] > 0 ? 0 : 1) * F + f1];
+                up += spin[v] > 0;
+              }
+              T re = (has0 ? z0 * swr[2 * f0] : (T)0) + (has1 ? z1 * swr[2 * f1] : (T)0);
+              T im = (has0 ? z0 * swr[2 * f0 + 1] : (T)0) + (has1 ? z1 * swr[2 * f1 + 1] : (T)0);
+              re = wsum(re);
+              im = wsum(im);
+              if (lane == 0) {
+                const int dn = N - up;
+                a.logpsi_out[((size_t)rec * a.C + ch) * 2] =
+                    (double)(re + (T)up * swr[2 * F] + (T)dn * swr[2 * (F + 1)] + sbr[0]);
+                a.logpsi_out[((size_t)rec * a.C + ch) * 2 + 1] =
+                    (double)(im + (T)up * swr[2 * F + 1] + (T)dn * swr[2 * (F + 1) + 1] + sbr[1]);
+              }
+            }
+          }
+        }
+      }
+    }
+    for (int v = lane; v < N; v += 32) a.chain_spins[ch * N + v] = spin[v];
+    if (lane == 0 && a.n_acc) a.n_acc[ch] += accepts;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------------
+struct MetroPlan {
+  int grid = 0;
+  int smem = 0;
+  int nwarps = 0;
+  int warp_elems = 0;
+  int off_dh[kMaxL + 1] = {0};
+  int off_dy[kMaxL + 1] = {0};
+  size_t ws_elems = 0;
+  size_t ws_bytes = 0;
+};
+
+template <typename T>
+static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, MetroPlan* p) {
+  if (m.L < 1 || m.F > 64) return GNA_ERR_UNSUPPORTED;
+  DeviceInfo di;
+  gna_status st = device_info(&di);
+  if (st != GNA_OK) return st;
+  const int F = m.F, L = m.L;
+  int o = 0;
+  for (int l = 0; l < L; ++l) {
+    p->off_dh[l] = o;
+    o += g->max_ball[l] * F;
+  }
+  for (int l = 1; l <= L; ++l) {
+    p->off_dy[l] = o;
+    o += g->max_ball[l] * F;
+  }
+  p->warp_elems = (o + 3) / 4 * 4;
+  const size_t param_elems = (size_t)2 * F * (F + 1) + F + 2 * F + (F + 2) * 2 + 2;
+  const size_t param_pad = (param_elems + 3) / 4 * 4;
+  auto smem_for = [&](int nw) {
+    return (param_pad + (size_t)nw * p->warp_elems) * sizeof(T) + (size_t)nw * ((m.N + 15) / 16 * 16);
+  };
+  int nw = kMetroMaxWarps;
+  while (nw > 0 && smem_for(nw) > (size_t)di.smem_optin - 1024) --nw;
+  if (nw < 2) return GNA_ERR_UNSUPPORTED;
+  p->nwarps = nw;
+  p->smem = (int)smem_for(nw);
+  GNA_CUDA_TRY(cudaFuncSetAttribute((const void*)k_metro_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem));
+  int occ = 0;
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_metro_warp<T>, 32 * nw, p->smem));
+  if (occ < 1) occ = 1;
+  int64_t grid = (int64_t)di.sms * occ;
+  const int64_t need = (C + nw - 1) / nw;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  p->grid = (int)grid;
+  p->ws_elems = (size_t)(L + 2) * m.N * F;
+  p->ws_bytes = align_up((size_t)grid * nw * p->ws_elems * sizeof(T));
+  return GNA_OK;
+}
+
+gna_status metro_workspace(const gna_graph* g, const Dims& m, int prec, int64_t C, size_t* bytes) {
+  if (C == 0) {
+    *bytes = 0;
+    return GNA_OK;
+  }
+  MetroPlan p;
+  gna_status st = prec == GNA_PREC_FP64 ? metro_plan<double>(g, m, C, &p) : metro_plan<float>(g, m, C, &p);
+  if (st != GNA_OK) return st;
+  *bytes = p.ws_bytes;
+  return GNA_OK;
+}
+
+template <typename T>
+static gna_status metro_launch_t(const MetroCall& mc, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  MetroPlan p;
+  gna_status st = metro_plan<T>(mc.g, mc.m, mc.C, &p);
+  if (st != GNA_OK) return st;
+  if (ws_bytes < p.ws_bytes || !ws) return GNA_ERR_WORKSPACE;
+  MetroArgs<T> a;
+  a.g = mc.g->d;
+  a.m = mc.m;
+  for (int l = 0; l <= kMaxL; ++l) {
+    a.maxball[l] = (l <= mc.m.L && l <= mc.g->d.Lmax) ? mc.g->max_ball[l] : 0;
+    a.off_dh[l] = p.off_dh[l];
+    a.off_dy[l] = p.off_dy[l];
+  }
+  a.warp_elems = p.warp_elems;
+  a.nwarps = p.nwarps;
+  a.theta = (const T*)mc.theta;
+  a.chain_spins = mc.chain_spins;
+  a.C = mc.C;
+  a.n_sweeps = mc.n_sweeps;
+  a.record_every = mc.record_every;
+  a.seed = mc.seed;
+  a.step0 = mc.step0;
+  a.samples_out = mc.samples_out;
+  a.logpsi_out = mc.logpsi_out;
+  a.n_acc = mc.n_acc;
+  a.trace = mc.trace;
+  a.gws = (T*)ws;
+  a.ws_elems = p.ws_elems;
+  k_metro_warp<T><<<p.grid, 32 * p.nwarps, p.smem, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+gna_status metro_run(const MetroCall& mc, int prec, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (mc.C == 0 || mc.n_sweeps == 0) return GNA_OK;
+  return prec == GNA_PREC_FP64 ? metro_launch_t<double>(mc, ws, ws_bytes, stream)
+                               : metro_launch_t<float>(mc, ws, ws_bytes, stream);
+}
+
+}  // namespace gna

@@ -228,6 +228,26 @@ def test_metropolis_decisions_given_uniforms_and_ratios(torch, prec):
     assert acc.cpu().numpy().sum() == tr[:, :, 1].sum()
 
 
+@pytest.mark.parametrize("prec", [gna.PREC_FP32, gna.PREC_FP64])
+def test_metropolis_kagome108_records_match_forward(torch, prec):
+    # Kagome 6x6x3, L = 4, F = 32: the sampler's recorded log Psi (from its incrementally
+    # updated pre-activations) equals a fresh forward of the recorded configurations
+    g = W.kagome(6)
+    F, L = 32, 4
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, prec, scale=0.3)
+    ch = torch.tensor(W.random_spins(g.n_sites, 40, seed=9), device="cuda")
+    samples, lpo, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, 3, 1, 11, 0, trace=True)
+    x = samples.cpu().numpy()
+    assert np.all((x > 0).sum(-1) == g.n_sites // 2)
+    assert acc.cpu().numpy().sum() > 0
+    for r in range(3):
+        want = gna.forward(graph, model, theta, samples[r].contiguous()).cpu().numpy()
+        _close(lpo[r].cpu().numpy(), want, 1e-10 if prec == gna.PREC_FP64 else 1e-5)
+    if prec == gna.PREC_FP64:
+        # and the oracle on a few of them
+        _close(lpo[-1].cpu().numpy()[:3], gcn.logpsi(th, F, L, Ah, x[-1][:3]), 1e-10)
+
+
 def test_metropolis_resume_is_bit_identical(torch):
     # counter-based randomness: 2 sweeps then 3 sweeps from step0 + 2N equals 5 sweeps at once
     g = W.kagome(2)

@@ -42,6 +42,7 @@ struct gna_graph {
   std::vector<int> h_row_ptr, h_col, h_edges, h_ball_size, h_ball_off;
   std::vector<double> h_J;
   std::vector<int> max_ball;  // [Lmax+1] max over bonds of |ball_l|
+  std::vector<int> max_span;  // [Lmax+1] max over bonds of sum of degrees over ball_l rows
   int max_deg = 0;
   std::vector<void*> allocations;
 };

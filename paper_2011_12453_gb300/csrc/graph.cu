@@ -20,7 +20,7 @@ struct HostGraph {
   std::vector<int> row_ptr, col, col_edge, edges;
   std::vector<float> wf;
   std::vector<double> wd, J;
-  std::vector<int> ball_off, ball_size, ball_vert, row_nbr, nbr_pos, max_ball;
+  std::vector<int> ball_off, ball_size, ball_vert, row_nbr, nbr_pos, max_ball, max_span;
 };
 
 gna_status validate(int32_t n_sites, int32_t n_edges, const int32_t* edges, const double* J,
@@ -82,6 +82,7 @@ void build(int n, int E, const int32_t* edges, const double* J, int Lmax, HostGr
   h->ball_off.assign(E + 1, 0);
   h->ball_size.assign((size_t)E * (Lmax + 1), 0);
   h->max_ball.assign(Lmax + 1, 0);
+  h->max_span.assign(Lmax + 1, 0);
   h->ball_vert.clear();
   h->row_nbr.clear();
   h->nbr_pos.clear();
@@ -110,8 +111,12 @@ void build(int n, int E, const int32_t* edges, const double* J, int Lmax, HostGr
       lo = hi;
       sz[l] = (int)order.size();
     }
-    for (int l = 0; l <= Lmax; ++l)
+    for (int l = 0; l <= Lmax; ++l) {
       if (sz[l] > h->max_ball[l]) h->max_ball[l] = sz[l];
+      int span = 0;
+      for (int r = 0; r < sz[l]; ++r) span += h->row_ptr[order[r] + 1] - h->row_ptr[order[r]];
+      if (span > h->max_span[l]) h->max_span[l] = span;
+    }
     h->ball_off[e] = (int)h->ball_vert.size();
     for (int r = 0; r < (int)order.size(); ++r) {
       int v = order[r];
@@ -185,6 +190,7 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   g->h_ball_off = h.ball_off;
   g->h_J = h.J;
   g->max_ball = h.max_ball;
+  g->max_span = h.max_span;
   for (int v = 0; v < h.n; ++v) g->max_deg = std::max(g->max_deg, h.row_ptr[v + 1] - h.row_ptr[v]);
   *out = g;
   return GNA_OK;

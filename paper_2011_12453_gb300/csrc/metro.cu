@@ -23,16 +23,19 @@
 
 namespace gna {
 
-constexpr int kMetroMaxWarps = 8;  // chains per CTA at most (fewer when shared memory is short)
+constexpr int kMetroMaxWarps = 16;  // chains per CTA at most (fewer when shared memory is short)
 
 template <typename T>
 struct MetroArgs {
   DevGraph g;
   Dims m;
   int maxball[kMaxL + 1];
-  int off_dh[kMaxL + 1];  // per-warp smem element offsets of dH^l rows (l < L)
-  int off_dy[kMaxL + 1];  // ... and of dY^l rows (l = 1..L)
-  int warp_elems;         // elements of T per warp in shared memory
+  int off_dh[kMaxL + 1];  // per-warp smem element offsets (elements of T) of dH^l rows, l < L
+  int off_dy[kMaxL + 1];  // workspace element offsets of dY^l rows (l = 1..L) in the warp slot
+  int off_x;              // per-warp smem element offset of the 4 staged dX rows (4 x 2F)
+  int off_meta;           // per-warp smem byte offset of the row metadata
+  int max_rows, max_span; // capacity of the metadata arrays (rows of ball_L, their neighbours)
+  int warp_bytes;         // shared-memory bytes per warp
   int nwarps;             // warps (chains in flight) per CTA
   const T* theta;
   int8_t* chain_spins;
@@ -43,7 +46,7 @@ struct MetroArgs {
   double* logpsi_out;
   int32_t* n_acc;
   double* trace;
-  T* gws;          // per warp slot: Y^1..Y^L [L][N][F] then two H scratch rows [2][N][F]
+  T* gws;          // per warp slot: Y^1..Y^L [L][N][F], two H scratch layers [2][N][F], dY rows
   size_t ws_elems; // elements per warp slot
 };
 
@@ -99,12 +102,18 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   T* semb = sb + F;                  // [2][F]
   T* swr = semb + 2 * F;             // [(F+2)][2]
   T* sbr = swr + (F + 2) * 2;        // [2]
-  T* wbase = sbr + 2;
   const size_t param_elems = (size_t)2 * F * ldw + F + 2 * F + (F + 2) * 2 + 2;
   const size_t param_pad = (param_elems + 3) / 4 * 4;
-  wbase = (T*)smem + param_pad;
-  T* wsm = wbase + (size_t)warp * a.warp_elems;               // this warp's dH / dY rows
-  int8_t* spin = (int8_t*)(wbase + (size_t)a.nwarps * a.warp_elems) + (size_t)warp * ((N + 15) / 16 * 16);
+  T* wbase = (T*)smem + param_pad;
+  unsigned char* wb = (unsigned char*)wbase + (size_t)warp * a.warp_bytes;
+  T* wsm = (T*)wb;                                   // this warp's dH rows and staged dX rows
+  T* sX = wsm + a.off_x;                             // [4][2F]
+  int* mv = (int*)(wb + a.off_meta);                 // vertex of ball row r
+  int* mdeg = mv + a.max_rows;                       // its degree
+  int* mnb = mdeg + a.max_rows;                      // offset of its neighbour entries
+  int* npos = mnb + a.max_rows;                      // per neighbour entry: position in the ball
+  T* nwt = (T*)(mv + ((3 * a.max_rows + a.max_span + 3) / 4 * 4));  // ... and normalised weight
+  int8_t* spin = (int8_t*)(nwt + a.max_span);
   const T* th = a.theta;
   for (int i = threadIdx.x; i < 2 * F * F; i += blockDim.x) sW[(i / F) * ldw + i % F] = th[m.oW + i];
   for (int i = threadIdx.x; i < F; i += blockDim.x) sb[i] = th[m.ob + i];
@@ -118,6 +127,7 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   T* Ybase = a.gws + (size_t)gwarp * a.ws_elems;  // Y^l at Ybase + (l-1)*N*F
   T* Hs0 = Ybase + (size_t)L * N * F;
   T* Hs1 = Hs0 + (size_t)N * F;
+  T* dYg = Ybase;  // dY^l rows at dYg + off_dy[l]
   const int f0 = lane, f1 = lane + 32;
   const bool has0 = f0 < F, has1 = f1 < F;
   const int64_t n_steps = (int64_t)a.n_sweeps * N;
@@ -202,56 +212,112 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
           }
           __syncwarp();
         }
+        // row metadata of ball_L(e): vertex, degree, neighbour positions and weights
+        const int RL = __ldg(bsz + L);
+        const int nb_base = __ldg(g.row_nbr + bo);
+        for (int r = lane; r < RL; r += 32) {
+          const int v = __ldg(g.ball_vert + bo + r);
+          const int k0 = __ldg(g.row_ptr + v), dg = __ldg(g.row_ptr + v + 1) - k0;
+          const int o = __ldg(g.row_nbr + bo + r) - nb_base;
+          mv[r] = v;
+          mdeg[r] = dg;
+          mnb[r] = o;
+          for (int t = 0; t < dg; ++t) {
+            npos[o + t] = __ldg(g.nbr_pos + nb_base + o + t);
+            nwt[o + t] = (T)__ldg(g.wd + k0 + t);
+          }
+        }
+        __syncwarp();
         T pre = 0, pim = 0;
         for (int l = 1; l <= L; ++l) {
           const int sprev = __ldg(bsz + l - 1), R = __ldg(bsz + l);
           const T* dprev = wsm + a.off_dh[l - 1];
           T* dcur = l < L ? wsm + a.off_dh[l] : nullptr;
-          T* dycur = wsm + a.off_dy[l];
+          T* dyl = dYg + a.off_dy[l];
           const T* Y = Ybase + (size_t)(l - 1) * N * F;
-          for (int r = 0; r < R; ++r) {
-            const int v = __ldg(g.ball_vert + bo + r);
-            const int nb0 = __ldg(g.row_nbr + bo + r);
-            const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
-            T ag0 = 0, ag1 = 0;
-            for (int kk = k0; kk < k1; ++kk) {
-              const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
-              if (p < sprev) {
-                const T w = (T)__ldg(g.wd + kk);
-                if (has0) ag0 += w * dprev[(size_t)p * F + f0];
-                if (has1) ag1 += w * dprev[(size_t)p * F + f1];
+          for (int rb = 0; rb < R; rb += 4) {
+            // stage dX = [A_hat dH^{l-1} ; dH^{l-1}] of rows rb..rb+3 (zeros past R)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int r = rb + q;
+              T ag0 = 0, ag1 = 0, sf0 = 0, sf1 = 0;
+              if (r < R) {
+                const int o = mnb[r], dg = mdeg[r];
+                for (int t = 0; t < dg; ++t) {
+                  const int p = npos[o + t];
+                  if (p < sprev) {
+                    const T w = nwt[o + t];
+                    if (has0) ag0 += w * dprev[(size_t)p * F + f0];
+                    if (has1) ag1 += w * dprev[(size_t)p * F + f1];
+                  }
+                }
+                if (r < sprev) {
+                  if (has0) sf0 = dprev[(size_t)r * F + f0];
+                  if (has1) sf1 = dprev[(size_t)r * F + f1];
+                }
+              }
+              T* x = sX + q * 2 * F;
+              if (has0) {
+                x[f0] = ag0;
+                x[F + f0] = sf0;
+              }
+              if (has1) {
+                x[f1] = ag1;
+                x[F + f1] = sf1;
               }
             }
-            T sf0 = 0, sf1 = 0;
-            if (r < sprev) {
-              if (has0) sf0 = dprev[(size_t)r * F + f0];
-              if (has1) sf1 = dprev[(size_t)r * F + f1];
-            }
-            T y0 = 0, y1 = 0;
-            for (int q = 0; q < F; ++q) {
-              const T av = __shfl_sync(0xffffffffu, q < 32 ? ag0 : ag1, q & 31);
-              const T sv = __shfl_sync(0xffffffffu, q < 32 ? sf0 : sf1, q & 31);
-              if (has0) y0 += av * sW[q * ldw + f0] + sv * sW[(F + q) * ldw + f0];
-              if (has1) y1 += av * sW[q * ldw + f1] + sv * sW[(F + q) * ldw + f1];
-            }
-            if (has0) {
-              const T d = dtanh(Y[(size_t)v * F + f0], y0);
-              dycur[(size_t)r * F + f0] = y0;
-              if (l < L)
-                dcur[(size_t)r * F + f0] = d;
-              else {
-                pre += d * swr[2 * f0];
-                pim += d * swr[2 * f0 + 1];
+            __syncwarp();
+            // dY = dX W for the 4 rows (lane: output columns f0, f1)
+            T y00 = 0, y10 = 0, y20 = 0, y30 = 0, y01 = 0, y11 = 0, y21 = 0, y31 = 0;
+            const T* x0 = sX;
+            const T* x1 = sX + 2 * F;
+            const T* x2 = sX + 4 * F;
+            const T* x3 = sX + 6 * F;
+#pragma unroll 4
+            for (int q = 0; q < 2 * F; ++q) {
+              const T xa = x0[q], xb = x1[q], xc = x2[q], xd = x3[q];
+              if (has0) {
+                const T w = sW[q * ldw + f0];
+                y00 += xa * w;
+                y10 += xb * w;
+                y20 += xc * w;
+                y30 += xd * w;
+              }
+              if (has1) {
+                const T w = sW[q * ldw + f1];
+                y01 += xa * w;
+                y11 += xb * w;
+                y21 += xc * w;
+                y31 += xd * w;
               }
             }
-            if (has1) {
-              const T d = dtanh(Y[(size_t)v * F + f1], y1);
-              dycur[(size_t)r * F + f1] = y1;
-              if (l < L)
-                dcur[(size_t)r * F + f1] = d;
-              else {
-                pre += d * swr[2 * f1];
-                pim += d * swr[2 * f1 + 1];
+            __syncwarp();
+            const T ys0[4] = {y00, y10, y20, y30};
+            const T ys1[4] = {y01, y11, y21, y31};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int r = rb + q;
+              if (r >= R) break;
+              const int v = mv[r];
+              if (has0) {
+                const T d = dtanh(Y[(size_t)v * F + f0], ys0[q]);
+                dyl[(size_t)r * F + f0] = ys0[q];
+                if (l < L)
+                  dcur[(size_t)r * F + f0] = d;
+                else {
+                  pre += d * swr[2 * f0];
+                  pim += d * swr[2 * f0 + 1];
+                }
+              }
+              if (has1) {
+                const T d = dtanh(Y[(size_t)v * F + f1], ys1[q]);
+                dyl[(size_t)r * F + f1] = ys1[q];
+                if (l < L)
+                  dcur[(size_t)r * F + f1] = d;
+                else {
+                  pre += d * swr[2 * f1];
+                  pim += d * swr[2 * f1 + 1];
+                }
               }
             }
           }
@@ -271,10 +337,10 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
           ++accepts;
           for (int l = 1; l <= L; ++l) {
             const int R = __ldg(bsz + l);
-            const T* dy = wsm + a.off_dy[l];
+            const T* dy = dYg + a.off_dy[l];
             T* Y = Ybase + (size_t)(l - 1) * N * F;
             for (int r = 0; r < R; ++r) {
-              const int v = __ldg(g.ball_vert + bo + r);
+              const int v = mv[r];
               if (has0) Y[(size_t)v * F + f0] += dy[(size_t)r * F + f0];
               if (has1) Y[(size_t)v * F + f1] += dy[(size_t)r * F + f1];
             }
@@ -333,9 +399,10 @@ struct MetroPlan {
   int grid = 0;
   int smem = 0;
   int nwarps = 0;
-  int warp_elems = 0;
+  int warp_bytes = 0;
   int off_dh[kMaxL + 1] = {0};
   int off_dy[kMaxL + 1] = {0};
+  int off_x = 0, off_meta = 0, max_rows = 0, max_span = 0;
   size_t ws_elems = 0;
   size_t ws_bytes = 0;
 };
@@ -347,21 +414,32 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
   gna_status st = device_info(&di);
   if (st != GNA_OK) return st;
   const int F = m.F, L = m.L;
+  // per-warp shared memory: dH rows (l < L), 4 staged dX rows, row metadata, spins
   int o = 0;
   for (int l = 0; l < L; ++l) {
     p->off_dh[l] = o;
     o += g->max_ball[l] * F;
   }
+  p->off_x = o;
+  o += 4 * 2 * F;
+  size_t bytes = (size_t)o * sizeof(T);
+  bytes = (bytes + 15) / 16 * 16;
+  p->off_meta = (int)bytes;
+  p->max_rows = g->max_ball[L];
+  p->max_span = g->max_span[L];
+  const int meta_ints = (3 * p->max_rows + p->max_span + 3) / 4 * 4;  // keeps the weights 16-byte aligned
+  bytes += (size_t)meta_ints * 4 + (size_t)p->max_span * sizeof(T) + (size_t)m.N;
+  p->warp_bytes = (int)((bytes + 15) / 16 * 16);
+  // per-warp workspace slot: Y^1..Y^L, two H scratch layers, dY^1..dY^L rows
+  size_t e = (size_t)(L + 2) * m.N * F;
   for (int l = 1; l <= L; ++l) {
-    p->off_dy[l] = o;
-    o += g->max_ball[l] * F;
+    p->off_dy[l] = (int)e;
+    e += (size_t)g->max_ball[l] * F;
   }
-  p->warp_elems = (o + 3) / 4 * 4;
+  p->ws_elems = (e + 31) / 32 * 32;
   const size_t param_elems = (size_t)2 * F * (F + 1) + F + 2 * F + (F + 2) * 2 + 2;
-  const size_t param_pad = (param_elems + 3) / 4 * 4;
-  auto smem_for = [&](int nw) {
-    return (param_pad + (size_t)nw * p->warp_elems) * sizeof(T) + (size_t)nw * ((m.N + 15) / 16 * 16);
-  };
+  const size_t param_bytes = (param_elems + 3) / 4 * 4 * sizeof(T);
+  auto smem_for = [&](int nw) { return param_bytes + (size_t)nw * p->warp_bytes; };
   int nw = kMetroMaxWarps;
   while (nw > 0 && smem_for(nw) > (size_t)di.smem_optin - 1024) --nw;
   if (nw < 2) return GNA_ERR_UNSUPPORTED;
@@ -376,7 +454,6 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   p->grid = (int)grid;
-  p->ws_elems = (size_t)(L + 2) * m.N * F;
   p->ws_bytes = align_up((size_t)grid * nw * p->ws_elems * sizeof(T));
   return GNA_OK;
 }
@@ -407,7 +484,11 @@ static gna_status metro_launch_t(const MetroCall& mc, void* ws, size_t ws_bytes,
     a.off_dh[l] = p.off_dh[l];
     a.off_dy[l] = p.off_dy[l];
   }
-  a.warp_elems = p.warp_elems;
+  a.off_x = p.off_x;
+  a.off_meta = p.off_meta;
+  a.max_rows = p.max_rows;
+  a.max_span = p.max_span;
+  a.warp_bytes = p.warp_bytes;
   a.nwarps = p.nwarps;
   a.theta = (const T*)mc.theta;
   a.chain_spins = mc.chain_spins;

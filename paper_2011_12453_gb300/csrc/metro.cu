@@ -51,11 +51,43 @@ struct MetroArgs {
 };
 
 __device__ __forceinline__ double m_tanh(double x) { return tanh(x); }
-__device__ __forceinline__ float m_tanh(float x) { return tanhf(x); }
+// float tanh: odd Taylor series through x^13 for |x| < 0.5 (truncation below 5e-7
+// relative), else sgn(x) (1 - e)/(1 + e) with e = exp(-2|x|).
+__device__ __forceinline__ float m_tanh(float x) {
+  const float ax = fabsf(x);
+  if (ax < 0.5f) {
+    const float x2 = x * x;
+    float p = 21844.f / 6081075.f;
+    p = fmaf(p, x2, -1382.f / 155925.f);
+    p = fmaf(p, x2, 62.f / 2835.f);
+    p = fmaf(p, x2, -17.f / 315.f);
+    p = fmaf(p, x2, 2.f / 15.f);
+    p = fmaf(p, x2, -1.f / 3.f);
+    return fmaf(p * x2, x, x);
+  }
+  const float e = __expf(-2.f * ax);
+  return copysignf(__fdividef(1.f - e, 1.f + e), x);
+}
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
 
 template <typename T>
 __device__ __forceinline__ T wsum(T v) {
@@ -96,13 +128,15 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   const int N = m.N, F = m.F, L = m.L, E = m.E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ldw = F + 1;
-  // block-shared parameters
+  // block-shared parameters: W (2F x F) and its transpose Wt (F x (2F + 4)) for 128-bit row loads
+  const int ldt = 2 * F + 4;
   T* sW = (T*)smem;                  // [2F][F+1]
-  T* sb = sW + 2 * F * ldw;          // [F]
+  T* sWt = sW + 2 * F * ldw;         // [F][2F+4]
+  T* sb = sWt + F * ldt;             // [F]
   T* semb = sb + F;                  // [2][F]
   T* swr = semb + 2 * F;             // [(F+2)][2]
   T* sbr = swr + (F + 2) * 2;        // [2]
-  const size_t param_elems = (size_t)2 * F * ldw + F + 2 * F + (F + 2) * 2 + 2;
+  const size_t param_elems = (size_t)2 * F * ldw + (size_t)F * ldt + F + 2 * F + (F + 2) * 2 + 2;
   const size_t param_pad = (param_elems + 3) / 4 * 4;
   T* wbase = (T*)smem + param_pad;
   unsigned char* wb = (unsigned char*)wbase + (size_t)warp * a.warp_bytes;
@@ -115,7 +149,10 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   T* nwt = (T*)(mv + ((3 * a.max_rows + a.max_span + 3) / 4 * 4));  // ... and normalised weight
   int8_t* spin = (int8_t*)(nwt + a.max_span);
   const T* th = a.theta;
-  for (int i = threadIdx.x; i < 2 * F * F; i += blockDim.x) sW[(i / F) * ldw + i % F] = th[m.oW + i];
+  for (int i = threadIdx.x; i < 2 * F * F; i += blockDim.x) {
+    sW[(i / F) * ldw + i % F] = th[m.oW + i];
+    sWt[(i % F) * ldt + i / F] = th[m.oW + i];
+  }
   for (int i = threadIdx.x; i < F; i += blockDim.x) sb[i] = th[m.ob + i];
   for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) semb[i] = m_tanh(th[m.oWe + i] + th[m.obe + i % F]);
   for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) swr[i] = th[m.owr + i];
@@ -267,28 +304,40 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
               }
             }
             __syncwarp();
-            // dY = dX W for the 4 rows (lane: output columns f0, f1)
+            // prefetch the cached pre-activations of the 4 rows (hidden behind the GEMM)
+            T yc0[4], yc1[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int r = rb + q < R ? rb + q : R - 1;
+              const T* yr = Y + (size_t)mv[r] * F;
+              yc0[q] = has0 ? yr[f0] : (T)0;
+              yc1[q] = has1 ? yr[f1] : (T)0;
+            }
+            // dY = dX W for the 4 rows (lane: output columns f0, f1), 4 inputs per load
             T y00 = 0, y10 = 0, y20 = 0, y30 = 0, y01 = 0, y11 = 0, y21 = 0, y31 = 0;
-            const T* x0 = sX;
-            const T* x1 = sX + 2 * F;
-            const T* x2 = sX + 4 * F;
-            const T* x3 = sX + 6 * F;
-#pragma unroll 4
-            for (int q = 0; q < 2 * F; ++q) {
-              const T xa = x0[q], xb = x1[q], xc = x2[q], xd = x3[q];
-              if (has0) {
-                const T w = sW[q * ldw + f0];
-                y00 += xa * w;
-                y10 += xb * w;
-                y20 += xc * w;
-                y30 += xd * w;
-              }
-              if (has1) {
-                const T w = sW[q * ldw + f1];
-                y01 += xa * w;
-                y11 += xb * w;
-                y21 += xc * w;
-                y31 += xd * w;
+            const T* wt0 = sWt + (size_t)(has0 ? f0 : 0) * ldt;
+            const T* wt1 = sWt + (size_t)(has1 ? f1 : 0) * ldt;
+#pragma unroll 2
+            for (int q = 0; q < 2 * F; q += 4) {
+              T xa[4], xb[4], xc[4], xd[4], wa[4], wb[4];
+              load4(sX + q, xa);
+              load4(sX + 2 * F + q, xb);
+              load4(sX + 4 * F + q, xc);
+              load4(sX + 6 * F + q, xd);
+              load4(wt0 + q, wa);
+              if (has1) load4(wt1 + q, wb);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                y00 += xa[u] * wa[u];
+                y10 += xb[u] * wa[u];
+                y20 += xc[u] * wa[u];
+                y30 += xd[u] * wa[u];
+                if (has1) {
+                  y01 += xa[u] * wb[u];
+                  y11 += xb[u] * wb[u];
+                  y21 += xc[u] * wb[u];
+                  y31 += xd[u] * wb[u];
+                }
               }
             }
             __syncwarp();
@@ -298,9 +347,8 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
             for (int q = 0; q < 4; ++q) {
               const int r = rb + q;
               if (r >= R) break;
-              const int v = mv[r];
               if (has0) {
-                const T d = dtanh(Y[(size_t)v * F + f0], ys0[q]);
+                const T d = dtanh(yc0[q], ys0[q]);
                 dyl[(size_t)r * F + f0] = ys0[q];
                 if (l < L)
                   dcur[(size_t)r * F + f0] = d;
@@ -310,7 +358,7 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
                 }
               }
               if (has1) {
-                const T d = dtanh(Y[(size_t)v * F + f1], ys1[q]);
+                const T d = dtanh(yc1[q], ys1[q]);
                 dyl[(size_t)r * F + f1] = ys1[q];
                 if (l < L)
                   dcur[(size_t)r * F + f1] = d;
@@ -437,7 +485,7 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
     e += (size_t)g->max_ball[l] * F;
   }
   p->ws_elems = (e + 31) / 32 * 32;
-  const size_t param_elems = (size_t)2 * F * (F + 1) + F + 2 * F + (F + 2) * 2 + 2;
+  const size_t param_elems = (size_t)2 * F * (F + 1) + (size_t)F * (2 * F + 4) + F + 2 * F + (F + 2) * 2 + 2;
   const size_t param_bytes = (param_elems + 3) / 4 * 4 * sizeof(T);
   auto smem_for = [&](int nw) { return param_bytes + (size_t)nw * p->warp_bytes; };
   int nw = kMetroMaxWarps;

@@ -279,6 +279,28 @@ def test_backward_parity(torch, prec, shared):
     _close(got, want, TOL[prec] * 10)
 
 
+def test_backward_matches_finite_differences_triangular144(torch):
+    # triangular 12x12, L = 4, F = 48, FP64: the hand-written backward against central
+    # differences (h = 1e-6) of sum_x cot_x . log Psi_x computed by the forward kernel
+    g = W.triangular(12, 12)
+    F, L = 48, 4
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, gna.PREC_FP64, scale=0.2)
+    s = torch.tensor(W.random_spins(g.n_sites, 6, seed=3), device="cuda")
+    cot = torch.tensor(np.random.default_rng(2).normal(size=(6, 2)), device="cuda")
+    grad = gna.backward(graph, model, theta, s, cot).cpu().numpy()
+    idx = np.random.default_rng(5).choice(model.num_params, 24, replace=False)
+    h = 1e-6
+    for k in idx:
+        tp = theta.clone()
+        tp[k] += h
+        tm = theta.clone()
+        tm[k] -= h
+        fp = (gna.forward(graph, model, tp, s) * cot).sum().item()
+        fm = (gna.forward(graph, model, tm, s) * cot).sum().item()
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, grad[k])
+
+
 def test_autograd_function_uses_library_backward(torch):
     g = W.kagome(2)
     F, L = 8, 2

@@ -39,7 +39,8 @@ namespace gna {
 static __device__ int s_tc_status;
 
 constexpr int kTcThreads = 512;
-constexpr int kTcGroups = kTcThreads / 128;  // warp groups (4 warps each)
+constexpr int kTcUnits = 2;                    // independent 256-thread units for bond groups
+constexpr int kTcUnitThreads = kTcThreads / kTcUnits;
 constexpr int kTmemCols = 128;
 constexpr uint32_t kWaitLimit = 1u << 26;            // try_wait iterations
 constexpr uint64_t kWaitNs = 2000000000ull;          // and at most 2 s of wall time
@@ -164,8 +165,11 @@ struct TcLayout {
   // region (shared or global) byte offsets
   uint64_t rcache16, rY, rnew16, rpart, region_bytes;
   uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
-  int T;                          // A tiles (TMEM holds T accumulators of F columns)
-  int G;                          // bonds per group
+  int T;                          // A tiles per unit (TMEM holds T accumulators of F columns per unit)
+  int G;                          // bonds per group (per unit)
+  uint32_t a_unit;                // bytes of one unit's A tiles
+  uint32_t int_unit, dbl_unit;    // per-unit slices of the int / double scratch (elements)
+  uint64_t new16_unit, part_unit; // per-unit slices of the dH rows and Delta partials (bytes)
 };
 
 struct TcArgs {
@@ -184,6 +188,8 @@ struct TcArgs {
   int region_in_smem;
 };
 
+__host__ inline int tc_tiles_per_unit(int F) { return F <= 32 ? 2 : 1; }
+
 __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int region_in_smem, TcLayout* t) {
   const int F = m.F, N = m.N, L = m.L;
   uint64_t o = 0;
@@ -193,18 +199,21 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     o += bytes;
     return (uint32_t)r;
   };
-  t->T = kTmemCols / F;
+  t->T = tc_tiles_per_unit(F);
   t->G = G;
+  t->a_unit = (uint32_t)t->T * 128 * 2 * F * 2;
   t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
-  t->oA = take((uint64_t)t->T * 128 * 2 * F * 2, 1024);
+  t->oA = take((uint64_t)kTcUnits * t->a_unit, 1024);
   t->obias = take(F * 4, 16);
   t->oemb = take(2 * F * 4, 16);
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
   t->ospin = take(N, 16);
-  t->oint = take(((uint64_t)m.E + G + (L + 1) * (G + 1) + 16) * 4, 16);
-  t->odbl = take((uint64_t)(2 * G + 16 + kTcThreads) * 8, 16);
-  t->obar = take(8, 8);
+  t->int_unit = (uint32_t)(G + (L + 1) * (G + 1) + 4);
+  t->oint = take(((uint64_t)m.E + 16 + (uint64_t)kTcUnits * t->int_unit) * 4, 16);
+  t->dbl_unit = (uint32_t)(2 * G + 4);
+  t->odbl = take((uint64_t)(16 + kTcThreads + kTcUnits * t->dbl_unit) * 8, 16);
+  t->obar = take(8 * kTcUnits, 8);
   t->oslot = take(4, 4);
   // region
   uint64_t r = 0;
@@ -222,8 +231,10 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     t->new16_off[l] = n16;
     n16 += (uint64_t)G * maxball[l] * ldh * 2;
   }
-  t->rnew16 = rtake(n16);
-  t->rpart = rtake((uint64_t)kTcGroups * t->T * 128 * 2 * 4);  // [warp group][row][Re, Im] partial Delta
+  t->new16_unit = (n16 + 15) / 16 * 16;
+  t->rnew16 = rtake((uint64_t)kTcUnits * t->new16_unit);
+  t->part_unit = (uint64_t)(kTcUnitThreads / 128) * t->T * 128 * 2 * 4;  // [warp group][row][Re, Im]
+  t->rpart = rtake((uint64_t)kTcUnits * t->part_unit);
   t->region_bytes = (r + 255) / 256 * 256;
   if (region_in_smem) {
     t->oregion = take(t->region_bytes, 16);
@@ -241,25 +252,42 @@ struct TcCtx {
   const TcArgs* a;
   int N, F, L, E, T, G;
   int ldh, ldy;  // row strides: BF16 feature rows, FP32 pre-activation rows
-  unsigned char* smem;
   __nv_bfloat16* Wt;
-  unsigned char* A;
   float *bias, *emb, *wr, *br;
   int8_t* spin;
-  int* sint;
-  double* sdbl;
-  uint64_t* bar;
-  uint32_t* slot;
+  int* list;     // antiparallel bonds of the configuration
+  double* sdbl;  // shared double scratch (readout)
   unsigned char* region;
-  uint32_t tbase;
-  uint32_t phase;
-  int* fail;  // shared flag
+  int* fail;     // shared flag
 };
 
-__device__ __forceinline__ unsigned char* a_row_chunk(const TcCtx& c, int q, int chunk) {
-  // 16-byte chunk `chunk` (k = 8*chunk .. 8*chunk+7) of row q of the stacked A tiles
+// A group of threads that runs gather -> MMA -> epilogue rounds on its own A tiles, TMEM
+// columns and mbarrier: the whole CTA (forward), or one of kTcUnits units that take
+// alternate bond groups so that one unit's waits overlap the other's work.
+struct Unit {
+  int tid, nthr, bar_id, nwg;  // thread index in the unit, its size, named barrier (0: whole CTA), warp groups
+  unsigned char* A;
+  uint32_t tbase;
+  uint64_t* bar;
+  uint32_t phase;              // meaningful in the unit's thread 0 (the waiter)
+  __nv_bfloat16* d16;          // this unit's dH rows
+  float* part;                 // this unit's Delta partials [nwg][T*128][2]
+  int* slot_e;                 // [G]
+  int* soff;                   // [(L+1)][G+1]
+  double* res;                 // [2G] Delta of each bond of the group
+};
+
+__device__ __forceinline__ void unit_sync(const Unit& u) {
+  if (u.bar_id == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(u.bar_id), "r"(u.nthr) : "memory");
+}
+
+__device__ __forceinline__ unsigned char* a_row_chunk(const Unit& u, int F, int q, int chunk) {
+  // 16-byte chunk `chunk` (k = 8*chunk .. 8*chunk+7) of row q of the unit's stacked A tiles
   const int tile = q >> 7, qq = q & 127;
-  return c.A + (size_t)tile * 128 * 4 * c.F + (size_t)(qq >> 3) * (32 * c.F) + chunk * 128 + (qq & 7) * 16;
+  return u.A + (size_t)tile * 128 * 4 * F + (size_t)(qq >> 3) * (32 * F) + chunk * 128 + (qq & 7) * 16;
 }
 
 __device__ __forceinline__ const __nv_bfloat16* cache16(const TcCtx& c, int l) {
@@ -273,10 +301,9 @@ __device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
 __device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
   return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.ldy;
 }
-__device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, int l) {
-  return (__nv_bfloat16*)(c.region + c.a->lay.rnew16 + c.a->lay.new16_off[l]);
+__device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, const Unit& u, int l) {
+  return (__nv_bfloat16*)((unsigned char*)u.d16 + c.a->lay.new16_off[l]);
 }
-__device__ __forceinline__ float* dpart(const TcCtx& c) { return (float*)(c.region + c.a->lay.rpart); }
 
 // acc[0..8) += w * bf16 row chunk at p (16 bytes)
 __device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat16* p) {
@@ -291,33 +318,33 @@ __device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat
   acc[7] += w * bf16hi(u.w);
 }
 
-// Issue the MMAs of nt tiles (thread 0), commit, and wait (bounded).  Returns false on
-// timeout (uniform across the CTA).
-__device__ bool run_mmas(TcCtx& c, int nt) {
+// Issue the MMAs of nt tiles (unit thread 0), commit, and wait (bounded).  Returns false on
+// timeout (uniform across the unit).
+__device__ bool run_mmas(const TcCtx& c, Unit& u, int nt) {
   fence_proxy_async();
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  unit_sync(u);
+  if (u.tid == 0) {
     tc_fence_after();
     const int F = c.F;
     const uint32_t idesc = idesc_bf16(128, F);
     const uint32_t sbo = 32 * F;
-    const uint32_t a0 = smem_u32(c.A), b0 = smem_u32(c.Wt);
+    const uint32_t a0 = smem_u32(u.A), b0 = smem_u32(c.Wt);
     for (int t = 0; t < nt; ++t) {
       for (int kb = 0; kb < (2 * F) / 16; ++kb) {
         const uint64_t ad = sdesc(a0 + t * 128 * 4 * F + kb * 256, 128, sbo);
         const uint64_t bd = sdesc(b0 + kb * 256, 128, sbo);
-        mma_bf16(c.tbase + t * F, ad, bd, idesc, kb > 0 ? 1u : 0u);
+        mma_bf16(u.tbase + t * F, ad, bd, idesc, kb > 0 ? 1u : 0u);
       }
     }
-    mma_commit(c.bar);
-    const bool ok = mbar_wait_bounded(c.bar, c.phase);
+    mma_commit(u.bar);
+    const bool ok = mbar_wait_bounded(u.bar, u.phase);
     if (!ok) {
       *c.fail = 1;
       atomicOr(&s_tc_status, 1);
     }
+    u.phase ^= 1u;
   }
-  c.phase ^= 1u;
-  __syncthreads();
+  unit_sync(u);
   tc_fence_after();
   return *c.fail == 0;
 }
@@ -325,18 +352,18 @@ __device__ bool run_mmas(TcCtx& c, int nt) {
 // Forward epilogue for rows [r0, r0 + R) of layer l: Y = acc + b.  l < L: H^l = tanh(Y)
 // stored BF16 (and Y in FP32 when the call needs the incremental step).  l == L: Y^L in
 // FP32, or, for the forward-only call, H^L = tanh(Y^L) in FP32 for the readout.
-__device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool keep_y) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r0, int l, bool keep_y) {
+  const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, ldh = c.ldh, ldy = c.ldy;
   __nv_bfloat16* h16 = l < L ? cache16w(c, l) + (size_t)r0 * ldh : nullptr;
   float* y32 = cacheY(c, l) + (size_t)r0 * ldy;
   for (int t = 0; t < nt; ++t) {
     const int q = t * 128 + q4 * 32 + lane;
-    for (int ch = wg; ch < F / 8; ch += kTcGroups) {
+    for (int ch = wg; ch < F / 8; ch += u.nwg) {
       const int col = ch * 8;
       float v[8];
-      tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), v);
+      tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), v);
       if (q < R) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] += c.bias[col + i];
@@ -363,18 +390,17 @@ __device__ void epilogue_fwd(const TcCtx& c, int nt, int R, int r0, int l, bool 
     }
   }
   tc_fence_before();
-  __syncthreads();
+  unit_sync(u);
 }
 
-// Forward of the configuration in c.spin: fills the cache (layers 0..L-1 BF16, L FP32).
-__device__ bool tc_forward(TcCtx& c) {
+// Forward of the configuration in c.spin (unit = whole CTA): fills the cache.
+__device__ bool tc_forward(const TcCtx& c, Unit& u) {
   const int N = c.N, F = c.F, L = c.L, ldh = c.ldh;
   const DevGraph& g = c.a->g;
-  // layer 0: embedding rows
   __nv_bfloat16* c0 = cache16w(c, 0);
-  for (int i = threadIdx.x; i < N * F; i += blockDim.x)
+  for (int i = u.tid; i < N * F; i += u.nthr)
     c0[(size_t)(i / F) * ldh + i % F] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
-  __syncthreads();
+  unit_sync(u);
   const int F8 = F / 8;
   const int rows_per_pass = c.T * 128;
   for (int l = 1; l <= L; ++l) {
@@ -383,7 +409,7 @@ __device__ bool tc_forward(TcCtx& c) {
       const int R = min(rows_per_pass, N - r0);
       const int nt = (R + 127) / 128;
       // one thread per (row, half): half 0 writes the message chunks, half 1 the self chunks
-      for (int idx = threadIdx.x; idx < 2 * R; idx += blockDim.x) {
+      for (int idx = u.tid; idx < 2 * R; idx += u.nthr) {
         const int q = idx >> 1, v = r0 + q;
         if ((idx & 1) == 0) {
           const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
@@ -395,16 +421,16 @@ __device__ bool tc_forward(TcCtx& c) {
             w.y = pack_bf16(acc[2], acc[3]);
             w.z = pack_bf16(acc[4], acc[5]);
             w.w = pack_bf16(acc[6], acc[7]);
-            *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = w;
+            *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
           }
         } else {
           for (int ch = 0; ch < F8; ++ch)
-            *reinterpret_cast<uint4*>(a_row_chunk(c, q, F8 + ch)) =
+            *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
                 *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
         }
       }
-      if (!run_mmas(c, nt)) return false;
-      epilogue_fwd(c, nt, R, r0, l, c.a->op == TC_ELOC);
+      if (!run_mmas(c, u, nt)) return false;
+      epilogue_fwd(c, u, nt, R, r0, l, c.a->op == TC_ELOC);
     }
   }
   return true;
@@ -413,7 +439,7 @@ __device__ bool tc_forward(TcCtx& c) {
 // log Psi readout from the FP32 last layer (valid in thread 0), deterministic order.
 __device__ void tc_readout(const TcCtx& c, double out[2]) {
   const int N = c.N, F = c.F;
-  float* red = (float*)(c.sdbl + 2 * c.G + 16);
+  float* red = (float*)(c.sdbl + 16);
   const float* HL = cacheY(c, c.L);  // holds H^L for the forward-only call
   const int parts = blockDim.x / F;
   const int f = threadIdx.x % F, part = threadIdx.x / F;
@@ -451,22 +477,22 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
   return k;
 }
 
-// dX rows of a bond group at layer l, gathered into the A tiles:
+// dX rows of a bond group at layer l, gathered into the unit's A tiles:
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
 // One thread per (row, half): half 0 writes the message chunks, half 1 the self chunks.
-__device__ void gather_delta(const TcCtx& c, int l, const int* slot_e, int nb, const int* soff) {
+__device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, G = c.G, ldh = c.ldh;
   const int F8 = F / 8;
-  const int* offp = soff + (l - 1) * (G + 1);
-  const int* offl = soff + l * (G + 1);
+  const int* offp = u.soff + (l - 1) * (G + 1);
+  const int* offl = u.soff + l * (G + 1);
   const int R = offl[nb];
-  const __nv_bfloat16* dp = new16(c, l - 1);
-  for (int idx = threadIdx.x; idx < 2 * R; idx += blockDim.x) {
+  const __nv_bfloat16* dp = new16(c, u, l - 1);
+  for (int idx = u.tid; idx < 2 * R; idx += u.nthr) {
     const int q = idx >> 1;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
-    const int e = slot_e[k];
+    const int e = u.slot_e[k];
     const int bo = __ldg(g.ball_off + e);
     const int sprev = offp[k + 1] - offp[k];
     const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh;
@@ -485,13 +511,13 @@ __device__ void gather_delta(const TcCtx& c, int l, const int* slot_e, int nb, c
         w.y = pack_bf16(acc[2], acc[3]);
         w.z = pack_bf16(acc[4], acc[5]);
         w.w = pack_bf16(acc[6], acc[7]);
-        *reinterpret_cast<uint4*>(a_row_chunk(c, q, ch)) = w;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
       }
     } else {
       for (int ch = 0; ch < F8; ++ch) {
         const uint4 w = r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh + ch * 8)
                                   : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(a_row_chunk(c, q, F8 + ch)) = w;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) = w;
       }
     }
   }
@@ -500,28 +526,27 @@ __device__ void gather_delta(const TcCtx& c, int l, const int* slot_e, int nb, c
 // dY in TMEM -> dH = t (1 - H^2) / (1 + H t), t = tanh(dY), for group rows [0, R) at layer
 // l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
 // columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
-__device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e, int nb, const int* soff) {
+__device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int nb) {
   const DevGraph& g = c.a->g;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, G = c.G, ldh = c.ldh, ldy = c.ldy;
-  const int* offl = soff + l * (G + 1);
+  const int* offl = u.soff + l * (G + 1);
   const int R = offl[nb];
-  __nv_bfloat16* dout = l < L ? new16(c, l) : nullptr;
+  __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
   const float* Yl = cacheY(c, l);
-  float* part = dpart(c);
   for (int t = 0; t < nt; ++t) {
     const int q = t * 128 + q4 * 32 + lane;
     int v = 0;
     if (q < R) {
       const int k = slot_of(offl, nb, q);
-      v = __ldg(g.ball_vert + __ldg(g.ball_off + slot_e[k]) + (q - offl[k]));
+      v = __ldg(g.ball_vert + __ldg(g.ball_off + u.slot_e[k]) + (q - offl[k]));
     }
     float pre = 0.f, pim = 0.f;
-    for (int ch = wg; ch < F / 8; ch += kTcGroups) {
+    for (int ch = wg; ch < F / 8; ch += u.nwg) {
       const int col = ch * 8;
       float dy[8];
-      tmem_ld8(c.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
+      tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
       if (q < R) {
         const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col);
         const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
@@ -557,66 +582,65 @@ __device__ void epilogue_delta(const TcCtx& c, int l, int nt, const int* slot_e,
       }
     }
     if (l == L && q < R) {
-      part[((size_t)wg * c.T * 128 + q) * 2] = pre;
-      part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
+      u.part[((size_t)wg * c.T * 128 + q) * 2] = pre;
+      u.part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
     }
   }
   tc_fence_before();
-  __syncthreads();
+  unit_sync(u);
 }
 
-// Incremental Delta log Psi of the bonds slot_e[0..nb): results in sdbl[2k], sdbl[2k+1].
-__device__ bool tc_group(TcCtx& c, const int* slot_e, int nb, int* soff) {
+// Incremental Delta log Psi of the unit's bonds slot_e[0..nb): results in res[2k], res[2k+1].
+__device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, L = c.L, G = c.G, Lm = g.Lmax;
-  if (threadIdx.x == 0) {
+  if (u.tid == 0) {
     for (int l = 0; l <= L; ++l) {
       int o = 0;
       for (int k = 0; k < nb; ++k) {
-        soff[l * (G + 1) + k] = o;
-        o += __ldg(g.ball_size + (size_t)slot_e[k] * (Lm + 1) + l);
+        u.soff[l * (G + 1) + k] = o;
+        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
       }
-      soff[l * (G + 1) + nb] = o;
+      u.soff[l * (G + 1) + nb] = o;
     }
   }
-  __syncthreads();
+  unit_sync(u);
   // layer 0: dH^0_i = emb(s_j) - emb(s_i), dH^0_j = -dH^0_i
-  __nv_bfloat16* d0 = new16(c, 0);
-  for (int i = threadIdx.x; i < nb * 2 * F; i += blockDim.x) {
+  __nv_bfloat16* d0 = new16(c, u, 0);
+  for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
     const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
-    const int e = slot_e[k];
+    const int e = u.slot_e[k];
     const int self = __ldg(g.edges + 2 * e + r), other = __ldg(g.edges + 2 * e + (1 - r));
     const float dv = c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f] - c.emb[(c.spin[self] > 0 ? 0 : 1) * F + f];
-    d0[(size_t)(soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
+    d0[(size_t)(u.soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
   }
-  __syncthreads();
+  unit_sync(u);
   for (int l = 1; l <= L; ++l) {
-    gather_delta(c, l, slot_e, nb, soff);
-    const int nt = (soff[l * (G + 1) + nb] + 127) / 128;
-    if (!run_mmas(c, nt)) return false;
-    epilogue_delta(c, l, nt, slot_e, nb, soff);
+    gather_delta(c, u, l, nb);
+    const int nt = (u.soff[l * (G + 1) + nb] + 127) / 128;
+    if (!run_mmas(c, u, nt)) return false;
+    epilogue_delta(c, u, l, nt, nb);
   }
   // Delta_k = sum over the bond's last-layer rows of the per-row partials (one warp per bond)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int* offL = soff + L * (G + 1);
-  const float* part = dpart(c);
+  const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
+  const int* offL = u.soff + L * (G + 1);
   const size_t wgs = (size_t)c.T * 128;
   for (int k = warp; k < nb; k += nwarps) {
     float dre = 0.f, dim = 0.f;
     for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
-      for (int w = 0; w < min(kTcGroups, F / 8); ++w) {
-        dre += part[(w * wgs + q) * 2];
-        dim += part[(w * wgs + q) * 2 + 1];
+      for (int w = 0; w < min(u.nwg, F / 8); ++w) {
+        dre += u.part[(w * wgs + q) * 2];
+        dim += u.part[(w * wgs + q) * 2 + 1];
       }
     }
     dre = warp_sum_t(dre);
     dim = warp_sum_t(dim);
     if (lane == 0) {
-      c.sdbl[2 * k] = (double)dre;
-      c.sdbl[2 * k + 1] = (double)dim;
+      u.res[2 * k] = (double)dre;
+      u.res[2 * k + 1] = (double)dim;
     }
   }
-  __syncthreads();
+  unit_sync(u);
   return true;
 }
 
@@ -624,6 +648,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_fail;
   __shared__ int s_count;
+  __shared__ double s_eu[2 * kTcUnits];
   TcCtx c;
   c.a = &a;
   c.N = a.m.N;
@@ -634,31 +659,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   c.G = a.lay.G;
   c.ldh = a.m.F + 8;
   c.ldy = a.m.F + 4;
-  c.smem = smem;
   c.Wt = (__nv_bfloat16*)(smem + a.lay.oWt);
-  c.A = smem + a.lay.oA;
   c.bias = (float*)(smem + a.lay.obias);
   c.emb = (float*)(smem + a.lay.oemb);
   c.wr = (float*)(smem + a.lay.owr);
   c.br = (float*)(smem + a.lay.obr);
   c.spin = (int8_t*)(smem + a.lay.ospin);
-  c.sint = (int*)(smem + a.lay.oint);
+  c.list = (int*)(smem + a.lay.oint);
   c.sdbl = (double*)(smem + a.lay.odbl);
-  c.bar = (uint64_t*)(smem + a.lay.obar);
-  c.slot = (uint32_t*)(smem + a.lay.oslot);
   c.region = a.region_in_smem ? smem + a.lay.oregion : a.gregion + (size_t)blockIdx.x * a.lay.region_bytes;
   c.fail = &s_fail;
-  c.phase = 0;
   const int F = c.F, N = c.N;
   const Dims& m = a.m;
   const float* th = a.theta;
+  uint64_t* bars = (uint64_t*)(smem + a.lay.obar);
+  uint32_t* slot = (uint32_t*)(smem + a.lay.oslot);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    mbar_init(c.bar, 1);
+    for (int h = 0; h < kTcUnits; ++h) mbar_init(bars + h, 1);
   }
   if ((threadIdx.x >> 5) == 0) {
-    tmem_alloc(c.slot, kTmemCols);
+    tmem_alloc(slot, kTmemCols);
     tmem_relinquish();
   }
   // W^T (n = output feature, k = input feature) in the canonical K-major layout
@@ -675,16 +697,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  c.tbase = *c.slot;
+  const uint32_t tmem = *slot;
 
-  int* list = c.sint;
-  int* slot_e = c.sint + c.E;
-  int* soff = slot_e + c.G;
+  // the whole CTA as one unit (forward), and this thread's bond-group unit
+  Unit whole;
+  whole.tid = threadIdx.x;
+  whole.nthr = blockDim.x;
+  whole.bar_id = 0;
+  whole.nwg = blockDim.x / 128;
+  whole.A = smem + a.lay.oA;
+  whole.tbase = tmem;
+  whole.bar = bars;
+  whole.phase = 0;
+  const int h = threadIdx.x / kTcUnitThreads;
+  Unit u;
+  u.tid = threadIdx.x % kTcUnitThreads;
+  u.nthr = kTcUnitThreads;
+  u.bar_id = 1 + h;
+  u.nwg = kTcUnitThreads / 128;
+  u.A = smem + a.lay.oA + (size_t)h * a.lay.a_unit;
+  u.tbase = tmem + (uint32_t)(h * c.T * F);
+  u.bar = bars + h;
+  u.phase = 0;
+  u.d16 = (__nv_bfloat16*)(c.region + a.lay.rnew16 + (size_t)h * a.lay.new16_unit);
+  u.part = (float*)(c.region + a.lay.rpart + (size_t)h * a.lay.part_unit);
+  u.slot_e = c.list + c.E + 16 + h * a.lay.int_unit;
+  u.soff = u.slot_e + c.G;
+  u.res = c.sdbl + 16 + kTcThreads + h * a.lay.dbl_unit;
+
   bool ok = true;
   for (int64_t b = blockIdx.x; b < a.B && ok; b += gridDim.x) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) c.spin[i] = a.spins[b * N + i];
     __syncthreads();
-    ok = tc_forward(c);
+    // unit 0 and the whole CTA share mbarrier 0: its waiter (thread 0) carries the phase
+    if (threadIdx.x == 0) whole.phase = u.phase;
+    ok = tc_forward(c, whole);
+    if (threadIdx.x == 0) u.phase = whole.phase;
     if (!ok) break;
     if (a.op == TC_FWD) {
       double lp[2];
@@ -711,7 +759,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
           d += __ldg(a.g.J + e) * 0.25 * (double)(si * sj);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, anti);
-        if (anti) list[count + __popc(mask & ((1u << lane) - 1u))] = e;
+        if (anti) c.list[count + __popc(mask & ((1u << lane) - 1u))] = e;
         count += __popc(mask);
       }
       d = warp_sum_t(d);
@@ -724,17 +772,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       for (int e = threadIdx.x; e < c.E; e += blockDim.x) a.dlogpsi[b * c.E + e] = 0.f;
     __syncthreads();
     const int na = s_count;
-    double er = diag, ei = 0.0;
-    for (int t0 = 0; t0 < na && ok; t0 += c.G) {
+    // unit h takes the bond groups h, h + kTcUnits, ...
+    double er = 0.0, ei = 0.0;
+    for (int t0 = h * c.G; t0 < na; t0 += kTcUnits * c.G) {
       const int nb = min(c.G, na - t0);
-      if (threadIdx.x < nb) slot_e[threadIdx.x] = list[t0 + threadIdx.x];
-      __syncthreads();
-      ok = tc_group(c, slot_e, nb, soff);
-      if (!ok) break;
-      if (threadIdx.x == 0) {
+      if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
+      unit_sync(u);
+      if (!tc_group(c, u, nb)) break;
+      if (u.tid == 0) {
         for (int k = 0; k < nb; ++k) {
-          const int e = slot_e[k];
-          const float dre = (float)c.sdbl[2 * k], dim = (float)c.sdbl[2 * k + 1];
+          const int e = u.slot_e[k];
+          const float dre = (float)u.res[2 * k], dim = (float)u.res[2 * k + 1];
           const float amp = expf(dre);
           float sn, cs;
           sincosf(dim, &sn, &cs);
@@ -744,20 +792,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
           if (a.dlogpsi) a.dlogpsi[b * c.E + e] = dre;
         }
       }
-      __syncthreads();
+      unit_sync(u);
     }
+    if (u.tid == 0) {
+      s_eu[2 * h] = er;
+      s_eu[2 * h + 1] = ei;
+    }
+    __syncthreads();
+    ok = s_fail == 0;
     if (threadIdx.x == 0 && ok) {
-      a.eloc[2 * b] = er;
-      a.eloc[2 * b + 1] = ei;
+      double re = diag, im = 0.0;
+      for (int hh = 0; hh < kTcUnits; ++hh) {
+        re += s_eu[2 * hh];
+        im += s_eu[2 * hh + 1];
+      }
+      a.eloc[2 * b] = re;
+      a.eloc[2 * b + 1] = im;
     }
     __syncthreads();
   }
   // teardown: on failure wait (bounded) for the MMAs in flight before freeing TMEM
-  if (!ok && threadIdx.x == 0) mbar_wait_bounded(c.bar, c.phase ^ 1u);  // the phase that timed out
+  if (!ok && u.tid == 0) mbar_wait_bounded(u.bar, u.phase ^ 1u);  // the phase that timed out
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(c.tbase, kTmemCols);
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------------
@@ -777,8 +836,9 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (st != GNA_OK) return st;
   if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
-  const int T = kTmemCols / m.F;
-  const size_t budget = (size_t)di.smem_optin - 1024;
+  const int T = tc_tiles_per_unit(m.F);
+  if (kTcUnits * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
+  const size_t budget = (size_t)di.smem_optin - 2048;
   int G = op == TC_ELOC ? (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1) : 1;
   if (G > 16) G = 16;
   if (G < 1) return GNA_ERR_UNSUPPORTED;  // one bond's last-layer rows exceed the TMEM tiles

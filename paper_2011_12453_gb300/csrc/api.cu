@@ -122,13 +122,16 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_ELOC, B, bytes);
       return simt_workspace(g, m, sp, 2, B, bytes);
     case GNA_OP_METROPOLIS: {
-      gna_status st = metro_workspace(g, m, sp, B, bytes);
+      gna_status st = metro_workspace(g, m, sp, B, 0, bytes);
       if (st != GNA_ERR_UNSUPPORTED) return st;
       return simt_workspace(g, m, sp, 3, B, bytes);
     }
-    case GNA_OP_METROPOLIS_LEARNED:
+    case GNA_OP_METROPOLIS_LEARNED: {
       if (g->max_deg > 16) return GNA_ERR_UNSUPPORTED;
+      gna_status st = metro_workspace(g, m, sp, B, 1, bytes);
+      if (st != GNA_ERR_UNSUPPORTED) return st;
       return simt_workspace(g, m, sp, 5, B, bytes);
+    }
     case GNA_OP_BACKWARD:
       return simt_workspace(g, m, sp, 4, B, bytes);
     case GNA_OP_ISGO_WEIGHTS:
@@ -259,14 +262,12 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
   sc.trace = trace;
   sc.prop = proposal_params;
   sc.prop_eps = proposal_eps;
-  if (!proposal_params) {
-    // warp-per-chain sampler when the model fits it, else one chain per CTA
-    size_t need = 0;
-    if (metro_workspace(g, sc.m, simt_prec(d), C, &need) == GNA_OK) {
-      MetroCall mc{g, sc.m, theta, chain_spins, C, n_sweeps, record_every, seed, step0,
-                   samples_out, logpsi_out, n_accepted, trace};
-      return metro_run(mc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
-    }
+  // warp-per-chain sampler when the model fits it, else one chain per CTA
+  size_t need = 0;
+  if (metro_workspace(g, sc.m, simt_prec(d), C, proposal_params != nullptr, &need) == GNA_OK) {
+    MetroCall mc{g, sc.m, theta, chain_spins, C, n_sweeps, record_every, seed, step0,
+                 samples_out, logpsi_out, n_accepted, trace, proposal_params, proposal_eps};
+    return metro_run(mc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
   }
   return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
 }

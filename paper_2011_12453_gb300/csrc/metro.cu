@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "metro.cuh"
+#include "prop.cuh"
 
 namespace gna {
 
@@ -36,6 +37,7 @@ struct MetroArgs {
   int off_meta;           // per-warp smem byte offset of the row metadata
   int max_rows, max_span; // capacity of the metadata arrays (rows of ball_L, their neighbours)
   int warp_bytes;         // shared-memory bytes per warp
+  int prop_rows;          // capacity of the proposal row arrays (4 x max degree, 0 without a network)
   int nwarps;             // warps (chains in flight) per CTA
   const T* theta;
   int8_t* chain_spins;
@@ -48,6 +50,8 @@ struct MetroArgs {
   double* trace;
   T* gws;          // per warp slot: Y^1..Y^L [L][N][F], two H scratch layers [2][N][F], dY rows
   size_t ws_elems; // elements per warp slot
+  const float* prop;  // learned proposal network or NULL (plain moves)
+  double prop_eps;
 };
 
 __device__ __forceinline__ double m_tanh(double x) { return tanh(x); }
@@ -110,6 +114,24 @@ __device__ __forceinline__ T dtanh(T y, T dy) {
 }
 
 template <typename T>
+__device__ inline bool m_accept_log(uint64_t r1, T log_ratio);
+template <>
+__device__ inline bool m_accept_log<double>(uint64_t r1, double log_ratio) {
+  return (double)(r1 >> 11) * 0x1.0p-53 < exp(log_ratio);
+}
+template <>
+__device__ inline bool m_accept_log<float>(uint64_t r1, float log_ratio) {
+  return (float)(r1 >> 40) * 0x1.0p-24f < expf(log_ratio);
+}
+
+// Row index in [r0, r1) whose partner is `other`.
+__device__ __forceinline__ int row_of(const int* ro, int r0, int r1, int other) {
+  for (int r = r0; r < r1; ++r)
+    if (ro[r] == other) return r;
+  return r0;
+}
+
+template <typename T>
 __device__ inline bool m_accept(uint64_t r1, T dre);
 template <>
 __device__ inline bool m_accept<double>(uint64_t r1, double dre) {
@@ -118,6 +140,148 @@ __device__ inline bool m_accept<double>(uint64_t r1, double dre) {
 template <>
 __device__ inline bool m_accept<float>(uint64_t r1, float dre) {
   return (float)(r1 >> 40) * 0x1.0p-24f < expf(2.0f * dre);
+}
+
+
+// ---- learned exchange proposal, evaluated by one warp ----------------------------------
+__device__ __forceinline__ int spin_x(const int8_t* sp, int v, int a, int b) {
+  return v == a ? sp[b] : (v == b ? sp[a] : sp[v]);
+}
+
+template <typename T>
+__device__ T nsum(const DevGraph& g, const int8_t* sp, int v, int a, int b) {
+  T acc = 0;
+  const int k1 = __ldg(g.row_ptr + v + 1);
+  for (int k = __ldg(g.row_ptr + v); k < k1; ++k) acc += (T)spin_x(sp, __ldg(g.col + k), a, b);
+  return acc;
+}
+
+// Features of the ordered pair (i, j) in s, or in s with (a, b) exchanged when a >= 0.
+template <typename T>
+__device__ void pair_phi(const DevGraph& g, const int8_t* sp, int i, int j, int a, int b, T* f) {
+  const int ki0 = __ldg(g.row_ptr + i), ki1 = __ldg(g.row_ptr + i + 1);
+  const int kj0 = __ldg(g.row_ptr + j), kj1 = __ldg(g.row_ptr + j + 1);
+  const int di = ki1 - ki0, dj = kj1 - kj0;
+  const T si = (T)spin_x(sp, i, a, b), sj = (T)spin_x(sp, j, a, b);
+  T Jij = 0, bi = 0, bj = 0;
+  int ci = 0, cj = 0;
+  for (int k = ki0; k < ki1; ++k) {
+    const int u = __ldg(g.col + k);
+    if (u == j) {
+      Jij = (T)__ldg(g.J + __ldg(g.col_edge + k));
+      continue;
+    }
+    bi += nsum<T>(g, sp, u, a, b) / (T)(__ldg(g.row_ptr + u + 1) - __ldg(g.row_ptr + u));
+    ++ci;
+  }
+  for (int k = kj0; k < kj1; ++k) {
+    const int u = __ldg(g.col + k);
+    if (u == i) continue;
+    bj += nsum<T>(g, sp, u, a, b) / (T)(__ldg(g.row_ptr + u + 1) - __ldg(g.row_ptr + u));
+    ++cj;
+  }
+  f[0] = si;
+  f[1] = sj;
+  f[2] = Jij;
+  f[3] = (T)1 / (T)di;
+  f[4] = (T)1 / (T)dj;
+  f[5] = (nsum<T>(g, sp, i, a, b) - sj) / (T)max(di - 1, 1);
+  f[6] = (nsum<T>(g, sp, j, a, b) - si) / (T)max(dj - 1, 1);
+  f[7] = ci ? bi / (T)ci : (T)0;
+  f[8] = cj ? bj / (T)cj : (T)0;
+}
+
+// Logits of rows r < n of (rc[r] -> ro[r]) evaluated in the state selected by rx[r]
+// (0: s, 1: s with (pa, pb) exchanged).  Returns the logit of row `lane` (and row lane+32).
+template <typename T>
+__device__ void warp_logits(const DevGraph& g, const int8_t* sp, const T* P, const int* rc, const int* ro,
+                            const int* rx, int n, int pa, int pb, T* out0, T* out1) {
+  const int lane = threadIdx.x & 31;
+  const T* W1 = P + kPropOW1;
+  const T* b1 = P + kPropOb1;
+  const T* W2 = P + kPropOW2;
+  const T* b2 = P + kPropOb2;
+  const T* w3 = P + kPropOw3;
+  T lg0 = 0, lg1 = 0;
+  for (int base = 0; base < n; base += 32) {
+    T f[kPropIn];
+    const int r = base + lane;
+    if (r < n) {
+      pair_phi<T>(g, sp, rc[r], ro[r], rx[r] ? pa : -1, rx[r] ? pb : -1, f);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPropIn; ++q) f[q] = 0;
+    }
+    const int cnt = min(32, n - base);
+    for (int rr = 0; rr < cnt; ++rr) {
+      // hidden layer 1 (units lane, lane + 32) of row base + rr
+      T z0 = b1[lane], z1 = b1[lane + 32];
+#pragma unroll
+      for (int q = 0; q < kPropIn; ++q) {
+        const T x = __shfl_sync(0xffffffffu, f[q], rr);
+        z0 += x * W1[q * kPropHid + lane];
+        z1 += x * W1[q * kPropHid + lane + 32];
+      }
+      const T h0 = m_tanh(z0), h1 = m_tanh(z1);
+      // hidden layer 2
+      T y0 = b2[lane], y1 = b2[lane + 32];
+      for (int q = 0; q < 32; ++q) {
+        const T xa = __shfl_sync(0xffffffffu, h0, q);
+        const T xb = __shfl_sync(0xffffffffu, h1, q);
+        y0 += xa * W2[q * kPropHid + lane] + xb * W2[(q + 32) * kPropHid + lane];
+        y1 += xa * W2[q * kPropHid + lane + 32] + xb * W2[(q + 32) * kPropHid + lane + 32];
+      }
+      T z = m_tanh(y0) * w3[lane] + m_tanh(y1) * w3[lane + 32];
+      z = wsum(z) + P[kPropOb3];
+      if (lane == rr) {
+        if (base == 0)
+          lg0 = z;
+        else
+          lg1 = z;
+      }
+    }
+  }
+  *out0 = lg0;
+  *out1 = lg1;
+}
+
+// Softmax probability of row `target_row` among rows [r0, r1) whose logits sit in lanes.
+template <typename T>
+__device__ T warp_softmax_prob(T lg0, T lg1, int r0, int r1, int target_row) {
+  const int lane = threadIdx.x & 31;
+  T zmax = -(T)INFINITY;
+  for (int r = r0; r < r1; ++r) {
+    const T z = __shfl_sync(0xffffffffu, r < 32 ? lg0 : lg1, r & 31);
+    zmax = z > zmax ? z : zmax;
+  }
+  T sum = 0, pt = 0;
+  for (int r = r0; r < r1; ++r) {
+    const T z = __shfl_sync(0xffffffffu, r < 32 ? lg0 : lg1, r & 31);
+    const T w = m_exp(z - zmax);
+    sum += w;
+    if (r == target_row) pt = w;
+  }
+  (void)lane;
+  return pt / sum;
+}
+
+// Appends the antiparallel neighbours of i (in CSR order) as rows (i -> u, x); all lanes
+// write the same values (warp-uniform), returns the new count.
+__device__ int push_rows(const DevGraph& g, const int8_t* sp, int i, int x, int pa, int pb, int* rc, int* ro, int* rx,
+                         int n) {
+  const int a = x ? pa : -1, b = x ? pb : -1;
+  const int si = spin_x(sp, i, a, b);
+  const int k1 = __ldg(g.row_ptr + i + 1);
+  for (int k = __ldg(g.row_ptr + i); k < k1; ++k) {
+    const int u = __ldg(g.col + k);
+    if (spin_x(sp, u, a, b) != si) {
+      rc[n] = i;
+      ro[n] = u;
+      rx[n] = x;
+      ++n;
+    }
+  }
+  return n;
 }
 
 template <typename T>
@@ -138,7 +302,9 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   T* sbr = swr + (F + 2) * 2;        // [2]
   const size_t param_elems = (size_t)2 * F * ldw + (size_t)F * ldt + F + 2 * F + (F + 2) * 2 + 2;
   const size_t param_pad = (param_elems + 3) / 4 * 4;
-  T* wbase = (T*)smem + param_pad;
+  T* sP = (T*)smem + param_pad;  // proposal network (when used)
+  const size_t prop_pad = a.prop ? ((size_t)kPropParams + 3) / 4 * 4 : 0;
+  T* wbase = sP + prop_pad;
   unsigned char* wb = (unsigned char*)wbase + (size_t)warp * a.warp_bytes;
   T* wsm = (T*)wb;                                   // this warp's dH rows and staged dX rows
   T* sX = wsm + a.off_x;                             // [4][2F]
@@ -147,7 +313,10 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   int* mnb = mdeg + a.max_rows;                      // offset of its neighbour entries
   int* npos = mnb + a.max_rows;                      // per neighbour entry: position in the ball
   T* nwt = (T*)(mv + ((3 * a.max_rows + a.max_span + 3) / 4 * 4));  // ... and normalised weight
-  int8_t* spin = (int8_t*)(nwt + a.max_span);
+  int* prc = (int*)(nwt + a.max_span);               // proposal rows: centre, partner, exchanged
+  int* pro = prc + a.prop_rows;
+  int* prx = pro + a.prop_rows;
+  int8_t* spin = (int8_t*)(prx + a.prop_rows);
   const T* th = a.theta;
   for (int i = threadIdx.x; i < 2 * F * F; i += blockDim.x) {
     sW[(i / F) * ldw + i % F] = th[m.oW + i];
@@ -157,6 +326,8 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
   for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) semb[i] = m_tanh(th[m.oWe + i] + th[m.obe + i % F]);
   for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) swr[i] = th[m.owr + i];
   if (threadIdx.x < 2) sbr[threadIdx.x] = th[m.obr + threadIdx.x];
+  if (a.prop)
+    for (int i = threadIdx.x; i < kPropParams; i += blockDim.x) sP[i] = (T)a.prop[i];
   __syncthreads();
 
   const int64_t gwarp = (int64_t)blockIdx.x * a.nwarps + warp;
@@ -213,26 +384,99 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
       __syncwarp();
     }
     int accepts = 0;
-    uint64_t w0 = 0, w1 = 0;  // Philox words r0, r1 of step (k0 + lane)
+    uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // Philox words of step (k0 + lane)
     for (int64_t k = 0; k < n_steps; ++k) {
       if ((k & 31) == 0) {
         const U64x4 w = philox4x64_10(a.seed, (uint64_t)ch, U64x4{a.step0 + (uint64_t)(k + lane), 0, 0, 0});
         w0 = w.x;
         w1 = w.y;
+        w2 = w.z;
+        w3 = w.w;
       }
       const uint64_t r0 = __shfl_sync(0xffffffffu, w0, (int)(k & 31));
       const uint64_t r1 = __shfl_sync(0xffffffffu, w1, (int)(k & 31));
-      const int e = (int)__umul64hi(r0, (uint64_t)E);
-      const int i = __ldg(g.edges + 2 * e), j = __ldg(g.edges + 2 * e + 1);
+      int e = -1, kind = 1;
+      bool move = false;
+      T logq = 0;
+      if (!a.prop) {
+        e = (int)__umul64hi(r0, (uint64_t)E);
+        move = spin[__ldg(g.edges + 2 * e)] != spin[__ldg(g.edges + 2 * e + 1)];
+      } else {
+        const uint64_t r2 = __shfl_sync(0xffffffffu, w2, (int)(k & 31));
+        const uint64_t r3 = __shfl_sync(0xffffffffu, w3, (int)(k & 31));
+        const T eps = (T)a.prop_eps;
+        int pi = -1, pj = -1, n = 0;
+        T pij = 0, lg0 = 0, lg1 = 0;
+        if ((double)(r3 >> 40) * 0x1.0p-24 < a.prop_eps) {
+          e = (int)__umul64hi(r0, (uint64_t)E);
+          pi = __ldg(g.edges + 2 * e);
+          pj = __ldg(g.edges + 2 * e + 1);
+          move = spin[pi] != spin[pj];
+          if (move) n = push_rows(g, spin, pi, 0, pi, pj, prc, pro, prx, 0);
+        } else {
+          kind = 2;
+          pi = (int)__umul64hi(r2, (uint64_t)N);
+          const int n1 = push_rows(g, spin, pi, 0, -1, -1, prc, pro, prx, 0);
+          __syncwarp();
+          if (n1 > 0) {
+            // the partner j ~ pi_i(. | s), by the categorical uniform (r3 mod 2^32) 2^-32
+            warp_logits<T>(g, spin, sP, prc, pro, prx, n1, -1, -1, &lg0, &lg1);
+            T zmax = -(T)INFINITY;
+            for (int r = 0; r < n1; ++r) {
+              const T z = __shfl_sync(0xffffffffu, r < 32 ? lg0 : lg1, r & 31);
+              zmax = z > zmax ? z : zmax;
+            }
+            T sum = 0;
+            for (int r = 0; r < n1; ++r) sum += m_exp(__shfl_sync(0xffffffffu, r < 32 ? lg0 : lg1, r & 31) - zmax);
+            const T uc = (T)((double)(r3 & 0xFFFFFFFFull) * 0x1.0p-32);
+            T cum = 0;
+            int pick = n1 - 1;
+            for (int r = 0; r < n1; ++r) {
+              const T pr = m_exp(__shfl_sync(0xffffffffu, r < 32 ? lg0 : lg1, r & 31) - zmax) / sum;
+              cum += pr;
+              if (uc < cum) {
+                pick = r;
+                pij = pr;
+                break;
+              }
+              if (r == n1 - 1) pij = pr;
+            }
+            pj = pro[pick];
+            const int k1 = __ldg(g.row_ptr + pi + 1);
+            for (int kk = __ldg(g.row_ptr + pi); kk < k1; ++kk)
+              if (__ldg(g.col + kk) == pj) e = __ldg(g.col_edge + kk);
+            move = true;
+          }
+          __syncwarp();
+        }
+        if (move) {
+          // the exact mixture proposal density both ways: q(s -> s') and q(s' -> s)
+          int g0 = n;  // rows [0, g0): cand(i, s) (plain moves only)
+          n = push_rows(g, spin, pj, 0, pi, pj, prc, pro, prx, n);
+          const int g1 = n;
+          n = push_rows(g, spin, pi, 1, pi, pj, prc, pro, prx, n);
+          const int g2 = n;
+          n = push_rows(g, spin, pj, 1, pi, pj, prc, pro, prx, n);
+          __syncwarp();
+          warp_logits<T>(g, spin, sP, prc, pro, prx, n, pi, pj, &lg0, &lg1);
+          const T p_ij = kind == 1 ? warp_softmax_prob<T>(lg0, lg1, 0, g0, row_of(pro, 0, g0, pj)) : pij;
+          const T p_ji = warp_softmax_prob<T>(lg0, lg1, g0, g1, row_of(pro, g0, g1, pi));
+          const T p_ij2 = warp_softmax_prob<T>(lg0, lg1, g1, g2, row_of(pro, g1, g2, pj));
+          const T p_ji2 = warp_softmax_prob<T>(lg0, lg1, g2, n, row_of(pro, g2, n, pi));
+          const T wl = ((T)1 - eps) / (T)N, wp = eps / (T)E;
+          logq = (T)(log((double)(wl * (p_ij2 + p_ji2) + wp)) - log((double)(wl * (p_ij + p_ji) + wp)));
+        }
+      }
       double* tr = a.trace ? a.trace + ((size_t)ch * n_steps + k) * 4 : nullptr;
-      if (spin[i] == spin[j]) {
+      if (!move) {
         if (tr && lane == 0) {
           tr[0] = (double)e;
           tr[1] = 0.0;
           tr[2] = __longlong_as_double(0x7ff8000000000000ll);
-          tr[3] = 1.0;
+          tr[3] = (double)kind;
         }
       } else {
+        const int i = __ldg(g.edges + 2 * e), j = __ldg(g.edges + 2 * e + 1);
         const int bo = __ldg(g.ball_off + e);
         const int* bsz = g.ball_size + (size_t)e * (g.Lmax + 1);
         // layer 0: dH^0 rows (i, j)
@@ -374,12 +618,20 @@ __global__ void __launch_bounds__(32 * kMetroMaxWarps) k_metro_warp(const MetroA
         const T dre = wsum(pre);
         const T dim = wsum(pim);
         (void)dim;
-        const bool acc = m_accept<T>(r1, dre);
+        T value;
+        bool acc;
+        if (a.prop) {
+          value = (T)2 * dre + logq;
+          acc = m_accept_log<T>(r1, value);
+        } else {
+          value = dre;
+          acc = m_accept<T>(r1, dre);
+        }
         if (tr && lane == 0) {
           tr[0] = (double)e;
           tr[1] = acc ? 1.0 : 0.0;
-          tr[2] = (double)dre;
-          tr[3] = 1.0;
+          tr[2] = (double)value;
+          tr[3] = (double)kind;
         }
         if (acc) {
           ++accepts;
@@ -450,14 +702,16 @@ struct MetroPlan {
   int warp_bytes = 0;
   int off_dh[kMaxL + 1] = {0};
   int off_dy[kMaxL + 1] = {0};
-  int off_x = 0, off_meta = 0, max_rows = 0, max_span = 0;
+  int off_x = 0, off_meta = 0, max_rows = 0, max_span = 0, prop_rows = 0;
   size_t ws_elems = 0;
   size_t ws_bytes = 0;
 };
 
 template <typename T>
-static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, MetroPlan* p) {
+static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, int with_prop, MetroPlan* p) {
   if (m.L < 1 || m.F > 64) return GNA_ERR_UNSUPPORTED;
+  if (with_prop && g->max_deg > 16) return GNA_ERR_UNSUPPORTED;
+  p->prop_rows = with_prop ? 4 * (g->max_deg > 0 ? g->max_deg : 1) : 0;
   DeviceInfo di;
   gna_status st = device_info(&di);
   if (st != GNA_OK) return st;
@@ -476,7 +730,7 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
   p->max_rows = g->max_ball[L];
   p->max_span = g->max_span[L];
   const int meta_ints = (3 * p->max_rows + p->max_span + 3) / 4 * 4;  // keeps the weights 16-byte aligned
-  bytes += (size_t)meta_ints * 4 + (size_t)p->max_span * sizeof(T) + (size_t)m.N;
+  bytes += (size_t)meta_ints * 4 + (size_t)p->max_span * sizeof(T) + (size_t)3 * p->prop_rows * 4 + (size_t)m.N;
   p->warp_bytes = (int)((bytes + 15) / 16 * 16);
   // per-warp workspace slot: Y^1..Y^L, two H scratch layers, dY^1..dY^L rows
   size_t e = (size_t)(L + 2) * m.N * F;
@@ -486,7 +740,7 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
   }
   p->ws_elems = (e + 31) / 32 * 32;
   const size_t param_elems = (size_t)2 * F * (F + 1) + (size_t)F * (2 * F + 4) + F + 2 * F + (F + 2) * 2 + 2;
-  const size_t param_bytes = (param_elems + 3) / 4 * 4 * sizeof(T);
+  const size_t param_bytes = ((param_elems + 3) / 4 * 4 + (with_prop ? ((size_t)kPropParams + 3) / 4 * 4 : 0)) * sizeof(T);
   auto smem_for = [&](int nw) { return param_bytes + (size_t)nw * p->warp_bytes; };
   int nw = kMetroMaxWarps;
   while (nw > 0 && smem_for(nw) > (size_t)di.smem_optin - 1024) --nw;
@@ -506,13 +760,14 @@ static gna_status metro_plan(const gna_graph* g, const Dims& m, int64_t C, Metro
   return GNA_OK;
 }
 
-gna_status metro_workspace(const gna_graph* g, const Dims& m, int prec, int64_t C, size_t* bytes) {
+gna_status metro_workspace(const gna_graph* g, const Dims& m, int prec, int64_t C, int with_prop, size_t* bytes) {
   if (C == 0) {
     *bytes = 0;
     return GNA_OK;
   }
   MetroPlan p;
-  gna_status st = prec == GNA_PREC_FP64 ? metro_plan<double>(g, m, C, &p) : metro_plan<float>(g, m, C, &p);
+  gna_status st = prec == GNA_PREC_FP64 ? metro_plan<double>(g, m, C, with_prop, &p)
+                                        : metro_plan<float>(g, m, C, with_prop, &p);
   if (st != GNA_OK) return st;
   *bytes = p.ws_bytes;
   return GNA_OK;
@@ -521,7 +776,7 @@ gna_status metro_workspace(const gna_graph* g, const Dims& m, int prec, int64_t 
 template <typename T>
 static gna_status metro_launch_t(const MetroCall& mc, void* ws, size_t ws_bytes, cudaStream_t stream) {
   MetroPlan p;
-  gna_status st = metro_plan<T>(mc.g, mc.m, mc.C, &p);
+  gna_status st = metro_plan<T>(mc.g, mc.m, mc.C, mc.prop != nullptr, &p);
   if (st != GNA_OK) return st;
   if (ws_bytes < p.ws_bytes || !ws) return GNA_ERR_WORKSPACE;
   MetroArgs<T> a;
@@ -537,6 +792,9 @@ static gna_status metro_launch_t(const MetroCall& mc, void* ws, size_t ws_bytes,
   a.max_rows = p.max_rows;
   a.max_span = p.max_span;
   a.warp_bytes = p.warp_bytes;
+  a.prop_rows = p.prop_rows;
+  a.prop = mc.prop;
+  a.prop_eps = mc.prop_eps;
   a.nwarps = p.nwarps;
   a.theta = (const T*)mc.theta;
   a.chain_spins = mc.chain_spins;

@@ -910,8 +910,10 @@ __global__ void __launch_bounds__(kThreads) k_metropolis(const SimtArgs<T> a) {
 }
 
 // Reverse mode of Eq. (gcn) and the readout; activations recomputed per sample.
+constexpr int kThreadsBwd = 512;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_backward(const SimtArgs<T> a) {
+__global__ void __launch_bounds__(kThreadsBwd, 1) k_backward(const SimtArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctx<T> c;
   make_ctx(a, c, smem);
@@ -973,28 +975,65 @@ __global__ void __launch_bounds__(kThreads) k_backward(const SimtArgs<T> a) {
         dY[i] = Gb[i] * ((T)1 - Hl[i] * Hl[i]);
       }
       __syncthreads();
-      // dW[k][g] += sum_v X[v][k] dY[v][g];  db[g] += sum_v dY[v][g]
+      // dW[k][g] += sum_v X[v][k] dY[v][g] (4 k per thread, two v streams);
+      // db[g] += sum_v dY[v][g]
       const size_t oW = m.oW + (size_t)(l - 1) * m.strideW;
       const size_t ob = m.ob + (size_t)(l - 1) * m.strideW;
-      for (int i = threadIdx.x; i < 2 * F * F + F; i += blockDim.x) {
-        T acc = 0;
-        if (i < 2 * F * F) {
-          const int k = i / F, gg = i % F;
-          for (int v = 0; v < N; ++v) acc += X[(size_t)v * 2 * F + k] * dY[(size_t)v * F + gg];
-          part[oW + i] += (double)acc;
-        } else {
-          const int gg = i - 2 * F * F;
-          for (int v = 0; v < N; ++v) acc += dY[(size_t)v * F + gg];
-          part[ob + gg] += (double)acc;
+      const int nkb = (2 * F + 3) / 4;  // blocks of 4 input features (the last may be partial)
+      for (int i = threadIdx.x; i < nkb * F; i += blockDim.x) {
+        const int k0 = (i / F) * 4, gg = i % F;
+        const int nq = min(4, 2 * F - k0);
+        T a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        int v = 0;
+        for (; v + 1 < N; v += 2) {
+          const T* x0 = X + (size_t)v * 2 * F + k0;
+          const T* x1 = x0 + 2 * F;
+          const T d0 = dY[(size_t)v * F + gg], d1 = dY[(size_t)(v + 1) * F + gg];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < nq) {
+              a0[q] += x0[q] * d0;
+              a1[q] += x1[q] * d1;
+            }
         }
+        if (v < N) {
+          const T* x0 = X + (size_t)v * 2 * F + k0;
+          const T d0 = dY[(size_t)v * F + gg];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < nq) a0[q] += x0[q] * d0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nq) part[oW + (size_t)(k0 + q) * F + gg] += (double)(a0[q] + a1[q]);
+      }
+      for (int gg = threadIdx.x; gg < F; gg += blockDim.x) {
+        T b0 = 0, b1 = 0;
+        int v = 0;
+        for (; v + 1 < N; v += 2) {
+          b0 += dY[(size_t)v * F + gg];
+          b1 += dY[(size_t)(v + 1) * F + gg];
+        }
+        if (v < N) b0 += dY[(size_t)v * F + gg];
+        part[ob + gg] += (double)(b0 + b1);
       }
       __syncthreads();
-      // dX[v][k] = sum_g dY[v][g] W[k][g]   (into X)
-      for (int i = threadIdx.x; i < N * 2 * F; i += blockDim.x) {
-        const int v = i / (2 * F), k = i % (2 * F);
-        T acc = 0;
-        for (int gg = 0; gg < F; ++gg) acc += dY[(size_t)v * F + gg] * c.sW[k * c.ldw + gg];
-        X[i] = acc;
+      // dX[v][k] = sum_g dY[v][g] W[k][g]   (into X; 4 rows per thread)
+      for (int i = threadIdx.x; i < ((N + 3) / 4) * 2 * F; i += blockDim.x) {
+        const int vb = (i / (2 * F)) * 4, k = i % (2 * F);
+        const int v1 = min(vb + 1, N - 1), v2 = min(vb + 2, N - 1), v3 = min(vb + 3, N - 1);
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int gg = 0; gg < F; ++gg) {
+          const T w = c.sW[k * c.ldw + gg];
+          s0 += dY[(size_t)vb * F + gg] * w;
+          s1 += dY[(size_t)v1 * F + gg] * w;
+          s2 += dY[(size_t)v2 * F + gg] * w;
+          s3 += dY[(size_t)v3 * F + gg] * w;
+        }
+        X[(size_t)vb * 2 * F + k] = s0;
+        if (vb + 1 < N) X[(size_t)(vb + 1) * 2 * F + k] = s1;
+        if (vb + 2 < N) X[(size_t)(vb + 2) * 2 * F + k] = s2;
+        if (vb + 3 < N) X[(size_t)(vb + 3) * 2 * F + k] = s3;
       }
       __syncthreads();
       // G^{l-1}_v = sum_u A_hat[v][u] dX[u][:F] + dX[v][F:]
@@ -1104,7 +1143,7 @@ gna_status simt_plan(const gna_graph* g, const Dims& m, int op, int64_t B, Plan*
   const void* kp = kernel_ptr<T>(op);
   GNA_CUDA_TRY(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem));
   int occ = 0;
-  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, kThreads, p->smem));
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, op == OP_BWD ? kThreadsBwd : kThreads, p->smem));
   if (occ < 1) occ = 1;
   int64_t grid = (int64_t)di.sms * occ;
   if (B < grid) grid = B;
@@ -1180,7 +1219,7 @@ gna_status simt_launch(const SimtCall& sc, void* ws, size_t ws_bytes, cudaStream
       k_metropolis<T><<<p.grid, kThreads, p.smem, stream>>>(a);
       break;
     case OP_BWD:
-      k_backward<T><<<p.grid, kThreads, p.smem, stream>>>(a);
+      k_backward<T><<<p.grid, kThreadsBwd, p.smem, stream>>>(a);
       GNA_CUDA_TRY(cudaGetLastError());
       k_reduce_partials<<<(sc.m.P + 255) / 256, 256, 0, stream>>>(a.partial, p.grid, sc.m.P, sc.grad);
       break;
@@ -1278,7 +1317,7 @@ static gna_status backward_static_launch(const SimtCall& sc, cudaStream_t stream
     w += align_up((size_t)grid * region_bytes);
   }
   a.partial = (double*)w;
-  k_backward<T><<<(int)grid, kThreads, p.smem, stream>>>(a);
+  k_backward<T><<<(int)grid, kThreadsBwd, p.smem, stream>>>(a);
   GNA_CUDA_TRY(cudaGetLastError());
   k_reduce_partials<<<(sc.m.P + 255) / 256, 256, 0, stream>>>(a.partial, (int)grid, sc.m.P, sc.grad);
   GNA_CUDA_TRY(cudaGetLastError());

@@ -13,8 +13,8 @@
 // store the new rows.  Feature rows are stored with padded strides (F + 8 BF16, F + 4
 // FP32) so that lanes reading rows of different sites do not share banks.
 //
-// Storage: cached layers H^0..H^{L-1} are BF16, as the GEMM consumes them; the FP32
-// pre-activations Y^1..Y^L are cached for the incremental step.
+// Storage: cached layers H^0..H^{L-1} are BF16, as the GEMM consumes them; for every FP32
+// pre-activation Y^1..Y^L the incremental step keeps copysign(exp(-2|Y|), Y).
 //
 // Incremental ratios propagate differences instead of recomputing rows.  Exchanging
 // s_i and s_j changes layer 0 by dH^0 (rows i and j only).  With X = [A_hat H ; H] and
@@ -141,6 +141,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+
+// The incremental step needs, per cached unit, only sgn(Y) and e = exp(-2|Y|): they are
+// stored together as copysign(e, Y).
+__device__ __forceinline__ float sexp(float y) { return copysignf(__expf(-2.f * fabsf(y)), y); }
 
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
@@ -296,8 +300,8 @@ __device__ __forceinline__ const __nv_bfloat16* cache16(const TcCtx& c, int l) {
 __device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
   return (__nv_bfloat16*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.ldh;
 }
-// FP32 pre-activation Y^l (l = 1..L) of every site; for the forward-only call the last
-// slot holds H^L instead.
+// Per site and layer l = 1..L: copysign(exp(-2|Y^l|), Y^l) for the incremental step (Y^l
+// the FP32 pre-activation); for the forward-only call the last slot holds H^L instead.
 __device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
   return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.ldy;
 }
@@ -370,8 +374,8 @@ __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r
         float4* yo = reinterpret_cast<float4*>(y32 + (size_t)q * ldy + col);
         if (l < L) {
           if (keep_y) {
-            yo[0] = make_float4(v[0], v[1], v[2], v[3]);
-            yo[1] = make_float4(v[4], v[5], v[6], v[7]);
+            yo[0] = make_float4(sexp(v[0]), sexp(v[1]), sexp(v[2]), sexp(v[3]));
+            yo[1] = make_float4(sexp(v[4]), sexp(v[5]), sexp(v[6]), sexp(v[7]));
           }
           uint4 w;
           w.x = pack_bf16(tanh_fast(v[0]), tanh_fast(v[1]));
@@ -380,8 +384,8 @@ __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r
           w.w = pack_bf16(tanh_fast(v[6]), tanh_fast(v[7]));
           *reinterpret_cast<uint4*>(h16 + (size_t)q * ldh + col) = w;
         } else if (keep_y) {
-          yo[0] = make_float4(v[0], v[1], v[2], v[3]);
-          yo[1] = make_float4(v[4], v[5], v[6], v[7]);
+          yo[0] = make_float4(sexp(v[0]), sexp(v[1]), sexp(v[2]), sexp(v[3]));
+          yo[1] = make_float4(sexp(v[4]), sexp(v[5]), sexp(v[6]), sexp(v[7]));
         } else {
           yo[0] = make_float4(tanhf(v[0]), tanhf(v[1]), tanhf(v[2]), tanhf(v[3]));
           yo[1] = make_float4(tanhf(v[4]), tanhf(v[5]), tanhf(v[6]), tanhf(v[7]));
@@ -500,11 +504,33 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
       const int v = __ldg(g.ball_vert + bo + r);
       const int nb0 = __ldg(g.row_nbr + bo + r);
       const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+      // the neighbours inside ball_{l-1} (the only nonzero dH^{l-1} rows), loaded once
+      const int dg = k1 - k0;
+      int pp[8];
+      float ww[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        pp[t] = -1;
+        ww[t] = 0.f;
+        if (t < dg) {
+          const int p = __ldg(g.nbr_pos + nb0 + t);
+          if (p < sprev) {
+            pp[t] = p;
+            ww[t] = __ldg(g.wf + k0 + t);
+          }
+        }
+      }
       for (int ch = 0; ch < F8; ++ch) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int kk = k0; kk < k1; ++kk) {
-          const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
-          if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * ldh + ch * 8);
+        if (dg <= 8) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (pp[t] >= 0) fma_chunk(acc, ww[t], drow + (size_t)pp[t] * ldh + ch * 8);
+        } else {
+          for (int kk = k0; kk < k1; ++kk) {
+            const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
+            if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * ldh + ch * 8);
+          }
         }
         uint4 w;
         w.x = pack_bf16(acc[0], acc[1]);
@@ -550,20 +576,25 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
       if (q < R) {
         const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col);
         const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
-        const float y[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float se[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         float d[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           // e = exp(-2|Y|): H = sgn(Y)(1-e)/(1+e), 1 - H^2 = 4e/(1+e)^2, and
           // dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t))
-          const float e = __expf(-2.f * fabsf(y[i]));
+          const float e = fabsf(se[i]);
+          const float sg = se[i] < 0.f ? -1.f : 1.f;
           const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
-          const float sg = y[i] < 0.f ? -1.f : 1.f;
           const float ope = 1.f + e;
           const float den = ope * (ope + sg * (1.f - e) * tt);
-          // den is small only when the unit swings across saturation: then dH is O(1)
-          // and the direct difference has no cancellation
-          d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(y[i] + dy[i]) - tanhf(y[i]);
+          if (den > 1e-3f) {
+            d[i] = __fdividef(4.f * e * tt, den);
+          } else {
+            // a unit swinging across saturation: dH is O(1) and the direct difference has
+            // no cancellation (Y recovered from e)
+            const float y = -0.5f * sg * __logf(e);
+            d[i] = tanhf(y + dy[i]) - tanhf(y);
+          }
         }
         if (l < L) {
           uint4 w;

@@ -36,9 +36,26 @@ sys.path.insert(0, ROOT)
 from paper_2011_12453_gb300 import workloads as W  # noqa: E402
 
 METRIC = "local-energy samples/s and ISGO step time vs plain FP32 GPU form at ≤1e-4 rel. energy"
-WORKLOAD = dict(workload="kagome_6x6x3_heisenberg", n_sites=108, n_bonds=216, L=4, F=32, chains=16384,
-                sweeps_per_step=1, theta_seed=0, spin_seed=1)
+# One step = one ISGO iteration: `recorded_sweeps` Metropolis sweeps of every chain (one
+# sample per chain per sweep) reused for `reuse` updates, each update = forward + incremental
+# local energy + ISGO weights + backward + SGD.  The default is the Kagome 108-site workload.
+WORKLOADS = {
+    "kagome108": dict(workload="kagome_6x6x3_heisenberg", lattice="kagome", size=6, n_sites=108, n_bonds=216, L=4,
+                      F=32, chains=16384, recorded_sweeps=1, reuse=1, proposal="plain", theta_seed=0, spin_seed=1,
+                      comparator_samples=16384),
+    "triangular144": dict(workload="triangular_12x12_heisenberg", lattice="triangular", size=12, n_sites=144,
+                          n_bonds=432, L=4, F=48, chains=16384, recorded_sweeps=4, reuse=10, proposal="plain",
+                          theta_seed=0, spin_seed=2, comparator_samples=4096),
+    "kagome432": dict(workload="kagome_12x12x3_heisenberg", lattice="kagome", size=12, n_sites=432, n_bonds=864, L=6,
+                      F=64, chains=16384, recorded_sweeps=16, reuse=10, proposal="learned", theta_seed=0, spin_seed=1,
+                      comparator_samples=1024),
+}
+WORKLOAD = WORKLOADS["kagome108"]
 L2_FLUSH_BYTES = 512 << 20
+
+
+def make_graph(wl):
+    return W.kagome(wl["size"]) if wl["lattice"] == "kagome" else W.triangular(wl["size"], wl["size"])
 
 
 def parse():
@@ -48,11 +65,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default=os.environ.get("GNA_BENCH_PREC", "auto"))
-    p.add_argument("--chains", type=int, default=WORKLOAD["chains"])
+    p.add_argument("--workload", default="kagome108", choices=sorted(WORKLOADS))
+    p.add_argument("--chains", type=int, default=None, help="override the workload's chain count")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--only", default=None, choices=["eloc", "eloc_full", "metropolis", "backward", "forward"],
                    help="time one call of the path alone (for profiling); prints a short JSON line")
-    return p.parse_args()
+    a = p.parse_args()
+    a.wl = dict(WORKLOADS[a.workload])
+    if a.chains is not None:
+        a.wl["chains"] = a.chains
+    return a
 
 
 # ---------------------------------------------------------------------------------
@@ -186,11 +208,12 @@ def _oracle_worker(args):
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["MKL_NUM_THREADS"] = "1"
-    F, L, n_per, seed = args
+    wl, n_per, seed = args
     from oracle import gcn, isgo
 
-    g = W.kagome(6)
-    th = W.random_theta(F, L, 0)
+    g = make_graph(wl)
+    F, L = wl["F"], wl["L"]
+    th = W.random_theta(F, L, wl["theta_seed"])
     Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
     s = W.random_spins(g.n_sites, n_per, seed)
     t = time.perf_counter()
@@ -199,7 +222,9 @@ def _oracle_worker(args):
     return n_per, time.perf_counter() - t
 
 
-def cpu_oracle_rate(n_per_worker=6, workers=None):
+def cpu_oracle_rate(wl, n_per_worker=6, workers=None):
+    """The FP64 oracle's forward + full-re-evaluation local energy + ISGO weights + backward
+    on a bounded sample of the workload's configurations, one process per core."""
     import multiprocessing as mp
 
     workers = workers or min(16, os.cpu_count() or 1)
@@ -210,7 +235,7 @@ def cpu_oracle_rate(n_per_worker=6, workers=None):
         ctx = mp.get_context("spawn")
         t0 = time.perf_counter()
         with ctx.Pool(workers) as pool:
-            res = pool.map(_oracle_worker, [(WORKLOAD["F"], WORKLOAD["L"], n_per_worker, 100 + w) for w in range(workers)])
+            res = pool.map(_oracle_worker, [(wl, n_per_worker, 100 + w) for w in range(workers)])
         wall = time.perf_counter() - t0
     finally:
         for k, v in env_keep.items():
@@ -221,10 +246,15 @@ def cpu_oracle_rate(n_per_worker=6, workers=None):
     n = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return {"value": n / busy, "unit": "samples/s", "cores": workers, "kind": "oracle",
-            "sample": f"{n} Kagome-108 configurations ({n_per_worker} per worker, {workers} spawn workers, "
+            "sample": f"{n} {wl['workload']} configurations ({n_per_worker} per worker, {workers} spawn workers, "
                       f"1 BLAS thread each): FP64 forward + full-re-evaluation local energy + ISGO weights + "
                       f"backward; rate = configurations / slowest worker's busy time",
             "wall_s": wall}
+
+
+def oracle_sample_size(wl):
+    """Configurations per worker for about 10-30 s of oracle work."""
+    return {"kagome108": 6, "triangular144": 2, "kagome432": 1}.get(wl.get("key", ""), 2)
 
 
 # ---------------------------------------------------------------------------------
@@ -235,19 +265,22 @@ def run_reference(a):
     ws, rank, _ = dist_info()
     if ws > 1 and rank != 0:
         return 0
+    wl = dict(a.wl, key=a.workload)
     per_step = []
     workers = min(16, os.cpu_count() or 1)
+    n_per = 2 if a.workload == "kagome108" else 1
     for k in range(a.warmup + a.steps):
-        r = cpu_oracle_rate(n_per_worker=2, workers=workers)
+        r = cpu_oracle_rate(wl, n_per_worker=n_per, workers=workers)
         if k >= a.warmup:
             per_step.append(r)
-    n = sum(2 * workers for _ in per_step)
-    t = sum(2 * workers / r["value"] for r in per_step)
+    n = sum(n_per * workers for _ in per_step)
+    t = sum(n_per * workers / r["value"] for r in per_step)
     value = n / t
+    cfg = {k: v for k, v in a.wl.items() if k != "comparator_samples"}
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000.0 * t / len(per_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": dict(WORKLOAD, l2="n/a (CPU)"),
+            "impl": "reference", "config": dict(cfg, l2="n/a (CPU)"),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
                              "sample": per_step[0]["sample"]},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -259,34 +292,74 @@ def run_reference(a):
 # our arm
 # ---------------------------------------------------------------------------------
 
+# DRAM bytes per sample of the dominant kernels from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch / the samples it processed), valid only for the source file
+# that was profiled: keyed by (workload, kernel) with the SHA-256 of that source.
+PROFILED_TRAFFIC = {}
+
+
+def _source_sha(rel):
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2011_12453_gb300", "csrc", rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profiled_traffic(workload, kernel, source, units):
+    rec = PROFILED_TRAFFIC.get((workload, kernel))
+    if rec is None or rec["sha256"] != _source_sha(source):
+        return None
+    return rec["bytes_per_unit"] * units
+
+
+def sweep_flops(g, F, L, ball, deg_of, spins_np, steps_per_chain):
+    """Expected algorithmic FLOPs of `steps_per_chain` plain exchange proposals per chain: the
+    bond is uniform over the edges, an antiparallel bond costs
+    sum_{l=1..L} |ball_l(e)| (4F^2 + 2 deg F) (the difference propagation), a parallel one
+    nothing; the antiparallel set is taken from the chains' recorded states (stationary
+    chains), plus one forward per chain for the launch's layer cache."""
+    N = g.n_sites
+    fwd = L * sum(4 * F * F + 2 * deg_of[v] * F for v in range(N))
+    deg_mean = float(np.mean(deg_of))
+    per_bond = np.array([sum(ball[e][l] for l in range(1, L + 1)) for e in range(g.n_edges)], dtype=np.float64)
+    per_bond *= 4 * F * F + 2 * deg_mean * F
+    anti = spins_np[:, g.edges[:, 0]] != spins_np[:, g.edges[:, 1]]
+    per_step = (anti * per_bond[None, :]).sum(axis=1) / g.n_edges
+    return float((fwd + steps_per_chain * per_step).sum())
+
+
 def run_ours(a):
     import torch
 
-    from paper_2011_12453_gb300 import build as B, gna
+    from paper_2011_12453_gb300 import build as B, gna, vmc
 
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
     init_dist("nccl" if ws > 1 else "gloo")
     B.build()
     dev = torch.device("cuda", local)
-    g = W.kagome(6)
-    F, L, C = WORKLOAD["F"], WORKLOAD["L"], a.chains
+    wl = a.wl
+    g = make_graph(wl)
+    F, L, C = wl["F"], wl["L"], wl["chains"]
+    S, K = wl["recorded_sweeps"], wl["reuse"]
+    N = g.n_sites
+    Bn = S * C
     prec_name = a.prec
     graph = gna.Graph.from_workload(g, L)
     if prec_name == "auto":
         prec_name = "bf16"
         try:
-            gna.workspace_size(graph, gna.Model(F, L, gna.PREC_BF16), gna.OP_ELOC_INCR, C)
+            gna.workspace_size(graph, gna.Model(F, L, gna.PREC_BF16), gna.OP_ELOC_INCR, Bn)
         except gna.GnaError:
             prec_name = "fp32"
     prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32}[prec_name]
     model = gna.Model(F, L, prec)
     model32 = gna.Model(F, L, gna.PREC_FP32)
-    theta = torch.tensor(W.random_theta(F, L, 0), dtype=torch.float32, device=dev)
-    chains = torch.tensor(W.random_spins(g.n_sites, C, 1 + 1000 * rank), device=dev)
+    theta = torch.tensor(W.random_theta(F, L, wl["theta_seed"]), dtype=torch.float32, device=dev)
+    chains = torch.tensor(W.random_spins(N, C, wl["spin_seed"] + 1000 * rank), device=dev)
     P = model.num_params
-    lp = torch.empty((C, 2), dtype=torch.float64, device=dev)
-    E = torch.empty((C, 2), dtype=torch.float64, device=dev)
+    lp = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
+    E = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
     grad = torch.empty(P, dtype=torch.float64, device=dev)
     acc = torch.zeros(C, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -294,64 +367,78 @@ def run_ours(a):
     lr = 1e-3
     seed = 12345 + rank
     state = {"step": 0}
-    n_sites = g.n_sites
+    prop = None
+    if wl["proposal"] == "learned":
+        prop = torch.tensor(W.random_proposal_params(1, 0.3), dtype=torch.float32, device=dev)
 
-    def step(ev=None):
-        # ev: list of 7 events recorded between the phases
-        t = state["step"]
-        if ev:
-            ev[0].record(stream)
-        samples, lp0, _, _ = gna.metropolis_sweep(graph, model, theta, chains, 1, 1, seed, t * n_sites, n_accepted=acc)
-        s = samples[0]
-        if ev:
-            ev[1].record(stream)
-        gna.forward(graph, model, theta, s, out=lp)
-        if ev:
-            ev[2].record(stream)
-        gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
-        if ev:
-            ev[3].record(stream)
-        cot, stats = gna.isgo_weights(lp, lp0[0], E)
-        if ev:
-            ev[4].record(stream)
-        gna.backward(graph, model, theta, s, cot, out=grad)
-        gna.sgd_update(model, theta, grad, lr)
-        if ev:
-            ev[5].record(stream)
+    def step(marks=None):
+        def mark(name):
+            if marks is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append((name, e))
+
+        mark("start")
+        samples, lp0, _, _ = gna.metropolis_sweep(graph, model, theta, chains, S, 1, seed, state["step"] * S * N,
+                                                  n_accepted=acc, proposal=prop, eps=0.1)
+        s = samples.view(Bn, N)
+        l0 = lp0.view(Bn, 2)
+        mark("metropolis_sweep")
+        stats = None
+        for _ in range(K):
+            gna.forward(graph, model, theta, s, out=lp)
+            mark("forward")
+            gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
+            mark("local_energy")
+            cot, stats = gna.isgo_weights(lp, l0, E)
+            mark("isgo_weights")
+            gna.backward(graph, model, theta, s, cot, out=grad)
+            gna.sgd_update(model, theta, grad, lr)
+            mark("backward_sgd")
         state["step"] += 1
         return s, stats
 
-    # burn-in + warm-up
+    # burn-in + warm-up (the learned proposal is trained on the burnt-in chains first)
+    if prop is not None:
+        gna.metropolis_sweep(graph, model, theta, chains, 2, 0, seed + 7, 0, records=False)
+        vmc.train_proposal(graph, model, theta, chains, prop, 50, 3e-3)
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
-    K = a.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    Ksteps = a.steps
+    marks = [[] for _ in range(Ksteps)]
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    for k in range(K):
+    for k in range(Ksteps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
-        s, stats = step(evs[k])
+        s, stats = step(marks[k])
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ph = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(5)] for k in range(K)])  # ms
+    names = ["metropolis_sweep", "forward", "local_energy", "isgo_weights", "backward_sgd"]
+    ph = np.zeros((Ksteps, len(names)))  # ms per step, summed over the reuse updates
+    for k in range(Ksteps):
+        for (_, e0), (nm, e1) in zip(marks[k][:-1], marks[k][1:]):
+            ph[k, names.index(nm)] += e0.elapsed_time(e1)
     step_ms = ph.sum(axis=1)
     t_total = max_over_ranks(float(step_ms.sum()) / 1000.0, dev)
-    value = ws * C * K / t_total
+    value = ws * Bn * K * Ksteps / t_total
     last_s = s.clone()
 
-    # energy agreement on the last step's samples: this path vs the plain FP32 full re-evaluation
-    E_ours = gna.local_energy(graph, model, theta, last_s, gna.ELOC_INCREMENTAL).cpu().numpy()
-    E_full = gna.local_energy(graph, model32, theta, last_s, gna.ELOC_FULL).cpu().numpy()
+    # energy agreement and comparator timing on a bounded subset of the last step's samples:
+    # this path's incremental local energy vs the plain FP32 full re-evaluation
+    nc = min(Bn, wl["comparator_samples"])
+    sub = last_s[:nc].contiguous()
+    E_ours = gna.local_energy(graph, model, theta, sub, gna.ELOC_INCREMENTAL).cpu().numpy()
+    E_full = gna.local_energy(graph, model32, theta, sub, gna.ELOC_FULL).cpu().numpy()
     rel = abs(E_ours[:, 0].mean() - E_full[:, 0].mean()) / abs(E_full[:, 0].mean())
     per_sample = np.abs(E_ours[:, 0] - E_full[:, 0]) / np.abs(E_full[:, 0]).clip(1e-12)
+    Esub = torch.empty((nc, 2), dtype=torch.float64, device=dev)
 
-    # comparator timing: FP32 full re-evaluation vs this path's incremental, same samples
     def time_call(fn, reps=3):
         ts = []
         for _ in range(reps):
@@ -364,14 +451,15 @@ def run_ours(a):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    t_full = time_call(lambda: gna.local_energy(graph, model32, theta, last_s, gna.ELOC_FULL, out=E), reps=2)
-    t_incr = float(np.median(ph[:, 2]))
+    t_full = time_call(lambda: gna.local_energy(graph, model32, theta, sub, gna.ELOC_FULL, out=Esub), reps=2)
+    t_incr_sub = time_call(lambda: gna.local_energy(graph, model, theta, sub, gna.ELOC_INCREMENTAL, out=Esub))
+    t_incr = float(np.median(ph[:, 2])) / K  # one local-energy launch over all Bn samples
 
     # end to end through the public API with host buffers: pinned chains in, statistics out
     host_chains = chains.cpu().pin_memory()
     host_stats = torch.empty(4, dtype=torch.float64).pin_memory()
     e2e_ms = []
-    for k in range(max(2, min(K, 5))):
+    for k in range(max(2, min(Ksteps, 5)) if K == 1 else 1):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -381,62 +469,75 @@ def run_ours(a):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = ws * C / (max_over_ranks(float(np.mean(e2e_ms)) / 1000.0, dev))
+    e2e_value = ws * Bn * K / (max_over_ranks(float(np.mean(e2e_ms)) / 1000.0, dev))
 
-    # roofline of the dominant kernel (the incremental local energy)
+    # roofline of the dominant kernel of the step (the sampler or the incremental local energy)
     spins_np = last_s.cpu().numpy()
-    deg = np.bincount(g.edges.ravel(), minlength=g.n_sites)
-    ball = gna.ball_sizes_host(g.n_sites, g.edges, L)
+    deg = np.bincount(g.edges.ravel(), minlength=N)
+    ball = gna.ball_sizes_host(N, g.edges, L)
     fl_incr = float(incremental_flops(g, F, L, ball, deg, spins_np).sum())
-    fl_full = float(full_flops(g, F, L, deg, spins_np).sum())
+    fl_full_sub = float(full_flops(g, F, L, deg, spins_np[:nc]).sum())
+    fl_sweep = sweep_flops(g, F, L, ball, deg, spins_np[(S - 1) * C:], S * N)
     peaks, peak_kind = measured_peaks()
-    if prec == gna.PREC_BF16:
-        peak = peaks["bf16_tflops_sustained"]
-        bound = "tensor"
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    t_sweep = float(np.median(ph[:, 0]))
+    if t_sweep >= K * t_incr:
+        kern = "k_metro_warp (gna_metropolis_sweep, %d sweeps)" % S
+        roof = {"bound": "alu", "achieved": fl_sweep / (t_sweep / 1000.0) / 1e12, "peak": alu_peak,
+                "unit": "TFLOP/s", "kernel": kern,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz (FP32 difference propagation)",
+                "flops_per_launch": fl_sweep,
+                "traffic": profiled_traffic(wl["workload"], "k_metro_warp", "metro.cu", C * S)}
+    elif prec == gna.PREC_BF16:
+        roof = {"bound": "tensor", "achieved": fl_incr / (t_incr / 1000.0) / 1e12,
+                "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "kernel": "k_tc (gna_local_energy incremental, BF16 tcgen05)",
+                "peak_source": peak_kind + " bf16_tflops_sustained", "flops_per_launch": fl_incr,
+                "traffic": profiled_traffic(wl["workload"], "k_tc", "tc.cu", Bn)}
     else:
-        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound = "alu"
-    achieved = fl_incr / (t_incr / 1000.0) / 1e12
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "gna_local_energy incremental (k_eloc_incr)",
-            "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz",
-            "flops_per_launch": fl_incr}
+        roof = {"bound": "alu", "achieved": fl_incr / (t_incr / 1000.0) / 1e12, "peak": alu_peak,
+                "unit": "TFLOP/s", "kernel": "k_eloc_incr (gna_local_energy incremental, FP32)",
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz", "flops_per_launch": fl_incr,
+                "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    other = {"local_energy_tflops": fl_incr / (t_incr / 1000.0) / 1e12,
+             "sweep_tflops": fl_sweep / (t_sweep / 1000.0) / 1e12}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        cpu = cpu_oracle_rate()
+        cpu = cpu_oracle_rate(dict(wl, key=a.workload), n_per_worker=oracle_sample_size(dict(wl, key=a.workload)))
     if rank == 0:
+        cfg = {k: v for k, v in wl.items() if k != "comparator_samples"}
         line = {
-            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": K, "warmup": a.warmup,
-            "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": Ksteps,
+            "warmup": a.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec_name, "data": "synthetic",
-            "config": dict(WORKLOAD, chains=C, l2="flushed between timed steps (512 MiB write)",
+            "config": dict(cfg, samples_per_step=Bn, l2="flushed between timed steps (512 MiB write)",
                            parallelism=f"replicas{ws}"),
-            "isgo_step_ms": float(ph[:, 1:].sum(axis=1).mean()),
-            "phases_ms": {n: float(ph[:, i].mean()) for i, n in
-                          enumerate(["metropolis_sweep", "forward", "local_energy", "isgo_weights",
-                                     "backward_sgd"])},
-            "comparator": {"eloc_incremental_samples_per_s": C / (t_incr / 1000.0),
-                           "eloc_fp32_full_samples_per_s": C / (t_full / 1000.0),
-                           "speedup": t_full / t_incr,
+            "isgo_step_ms": float(ph[:, 1:].sum(axis=1).mean()) / K,
+            "phases_ms": {n: float(ph[:, i].mean()) for i, n in enumerate(names)},
+            "comparator": {"samples": nc,
+                           "eloc_incremental_samples_per_s": nc / (t_incr_sub / 1000.0),
+                           "eloc_fp32_full_samples_per_s": nc / (t_full / 1000.0),
+                           "speedup": t_full / t_incr_sub,
                            "energy_rel_diff_mean": float(rel),
                            "energy_rel_diff_per_sample_max": float(per_sample.max()),
-                           "fp32_full_tflops": fl_full / (t_full / 1000.0) / 1e12},
+                           "fp32_full_tflops": fl_full_sub / (t_full / 1000.0) / 1e12},
             "roofline": roof,
+            "other_kernels": other,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(C * g.n_sites),
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(C * N),
                     "d2h_bytes_per_step": 32},
-            "gpu_launches": int(K * 10),
+            "gpu_launches": int(Ksteps * (1 + 9 * K)),
             "clocks": clk,
-            "acceptance": float(acc.sum().item()) / max(1, (state["step"]) * C * g.n_sites),
+            "acceptance": float(acc.sum().item()) / max(1, state["step"] * S * C * N),
         }
         print(json.dumps(line))
     return 0
 
 
 def run_only(a):
-    """One operation of the step alone, W + K launches on the same workload."""
+    """One operation of the step alone, W + K launches on the workload's chains."""
     import torch
 
     from paper_2011_12453_gb300 import build as B, gna
@@ -444,14 +545,15 @@ def run_only(a):
     B.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    g = W.kagome(6)
-    F, L, C = WORKLOAD["F"], WORKLOAD["L"], a.chains
+    wl = a.wl
+    g = make_graph(wl)
+    F, L, C = wl["F"], wl["L"], wl["chains"]
     prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32, "auto": gna.PREC_BF16}[a.prec]
     graph = gna.Graph.from_workload(g, L)
     model = gna.Model(F, L, prec)
     model32 = gna.Model(F, L, gna.PREC_FP32)
-    theta = torch.tensor(W.random_theta(F, L, 0), dtype=torch.float32, device=dev)
-    spins = torch.tensor(W.random_spins(g.n_sites, C, 1), device=dev)
+    theta = torch.tensor(W.random_theta(F, L, wl["theta_seed"]), dtype=torch.float32, device=dev)
+    spins = torch.tensor(W.random_spins(g.n_sites, C, wl["spin_seed"]), device=dev)
     cot = torch.randn(C, 2, dtype=torch.float64, device=dev)
     out = torch.empty((C, 2), dtype=torch.float64, device=dev)
 
@@ -478,8 +580,8 @@ def run_only(a):
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
-    print(json.dumps({"only": a.only, "prec": a.prec, "chains": C, "ms": ts, "median_ms": float(np.median(ts)),
-                      "samples_per_s": C / (float(np.median(ts)) / 1000.0)}))
+    print(json.dumps({"only": a.only, "workload": wl["workload"], "prec": a.prec, "chains": C, "ms": ts,
+                      "median_ms": float(np.median(ts)), "samples_per_s": C / (float(np.median(ts)) / 1000.0)}))
     return 0
 
 

@@ -122,6 +122,10 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_ELOC, B, bytes);
       return simt_workspace(g, m, sp, 2, B, bytes);
     case GNA_OP_METROPOLIS: {
+      if (d->prec == GNA_PREC_BF16) {
+        gna_status st = tcm_workspace(g, m, B, bytes);
+        if (st != GNA_ERR_UNSUPPORTED) return st;
+      }
       gna_status st = metro_workspace(g, m, sp, B, 0, bytes);
       if (st != GNA_ERR_UNSUPPORTED) return st;
       return simt_workspace(g, m, sp, 3, B, bytes);
@@ -262,8 +266,14 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
   sc.trace = trace;
   sc.prop = proposal_params;
   sc.prop_eps = proposal_eps;
-  // warp-per-chain sampler when the model fits it, else one chain per CTA
+  // BF16 models, plain moves: the tensor-core sampler; otherwise the warp-per-chain sampler
+  // when the model fits it, else one chain per CTA
   size_t need = 0;
+  if (d->prec == GNA_PREC_BF16 && !proposal_params && tcm_workspace(g, sc.m, C, &need) == GNA_OK) {
+    TcmCall tc{g, sc.m, (const float*)theta, chain_spins, C, n_sweeps, record_every, seed, step0,
+               samples_out, logpsi_out, n_accepted, trace};
+    return tcm_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
   if (metro_workspace(g, sc.m, simt_prec(d), C, proposal_params != nullptr, &need) == GNA_OK) {
     MetroCall mc{g, sc.m, theta, chain_spins, C, n_sweeps, record_every, seed, step0,
                  samples_out, logpsi_out, n_accepted, trace, proposal_params, proposal_eps};

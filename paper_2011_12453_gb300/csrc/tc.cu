@@ -39,9 +39,8 @@ namespace gna {
 static __device__ int s_tc_status;
 
 constexpr int kTcThreads = 512;
-constexpr int kTcUnits = 2;                    // independent 256-thread units for bond groups
-constexpr int kTcUnitThreads = kTcThreads / kTcUnits;
-constexpr int kTmemCols = 128;
+constexpr int kTcMaxUnits = 4;  // independent units (2 of 256 or 4 of 128 threads) for bond groups
+constexpr int kTmemCols = 256;
 constexpr uint32_t kWaitLimit = 1u << 26;            // try_wait iterations
 constexpr uint64_t kWaitNs = 2000000000ull;          // and at most 2 s of wall time
 
@@ -170,10 +169,12 @@ struct TcLayout {
   uint64_t rcache16, rY, rnew16, rpart, region_bytes;
   uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
   int T;                          // A tiles per unit (TMEM holds T accumulators of F columns per unit)
+  int units;                      // bond-group units per CTA
   int G;                          // bonds per group (per unit)
   uint32_t a_unit;                // bytes of one unit's A tiles
   uint32_t int_unit, dbl_unit;    // per-unit slices of the int / double scratch (elements)
   uint64_t new16_unit, part_unit; // per-unit slices of the dH rows and Delta partials (bytes)
+  uint64_t rstate, state_unit;    // sampler only: per-unit chain-pool state (bytes)
 };
 
 struct TcArgs {
@@ -192,6 +193,9 @@ struct TcArgs {
   int region_in_smem;
 };
 
+// F <= 32: two 256-thread units with two 128-row tiles each; wider features: four 128-thread
+// units with one tile each (more independent rounds in flight per SM).
+__host__ inline int tc_units(int F) { return F <= 32 ? 2 : 4; }
 __host__ inline int tc_tiles_per_unit(int F) { return F <= 32 ? 2 : 1; }
 
 __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int region_in_smem, TcLayout* t) {
@@ -204,20 +208,22 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     return (uint32_t)r;
   };
   t->T = tc_tiles_per_unit(F);
+  t->units = tc_units(F);
+  const int U = t->units;
   t->G = G;
   t->a_unit = (uint32_t)t->T * 128 * 2 * F * 2;
   t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
-  t->oA = take((uint64_t)kTcUnits * t->a_unit, 1024);
+  t->oA = take((uint64_t)U * t->a_unit, 1024);
   t->obias = take(F * 4, 16);
   t->oemb = take(2 * F * 4, 16);
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
   t->ospin = take(N, 16);
   t->int_unit = (uint32_t)(G + (L + 1) * (G + 1) + 4);
-  t->oint = take(((uint64_t)m.E + 16 + (uint64_t)kTcUnits * t->int_unit) * 4, 16);
+  t->oint = take(((uint64_t)m.E + 16 + (uint64_t)U * t->int_unit) * 4, 16);
   t->dbl_unit = (uint32_t)(2 * G + 4);
-  t->odbl = take((uint64_t)(16 + kTcThreads + kTcUnits * t->dbl_unit) * 8, 16);
-  t->obar = take(8 * kTcUnits, 8);
+  t->odbl = take((uint64_t)(16 + kTcThreads + U * t->dbl_unit) * 8, 16);
+  t->obar = take(8 * U, 8);
   t->oslot = take(4, 4);
   // region
   uint64_t r = 0;
@@ -236,9 +242,9 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
     n16 += (uint64_t)G * maxball[l] * ldh * 2;
   }
   t->new16_unit = (n16 + 15) / 16 * 16;
-  t->rnew16 = rtake((uint64_t)kTcUnits * t->new16_unit);
-  t->part_unit = (uint64_t)(kTcUnitThreads / 128) * t->T * 128 * 2 * 4;  // [warp group][row][Re, Im]
-  t->rpart = rtake((uint64_t)kTcUnits * t->part_unit);
+  t->rnew16 = rtake((uint64_t)U * t->new16_unit);
+  t->part_unit = (uint64_t)(kTcThreads / U / 128) * t->T * 128 * 2 * 4;  // [warp group][row][Re, Im]
+  t->rpart = rtake((uint64_t)U * t->part_unit);
   t->region_bytes = (r + 255) / 256 * 256;
   if (region_in_smem) {
     t->oregion = take(t->region_bytes, 16);
@@ -266,7 +272,7 @@ struct TcCtx {
 };
 
 // A group of threads that runs gather -> MMA -> epilogue rounds on its own A tiles, TMEM
-// columns and mbarrier: the whole CTA (forward), or one of kTcUnits units that take
+// columns and mbarrier: the whole CTA (forward), or one of the units that take
 // alternate bond groups so that one unit's waits overlap the other's work.
 struct Unit {
   int tid, nthr, bar_id, nwg;  // thread index in the unit, its size, named barrier (0: whole CTA), warp groups
@@ -412,26 +418,20 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
     for (int r0 = 0; r0 < N; r0 += rows_per_pass) {
       const int R = min(rows_per_pass, N - r0);
       const int nt = (R + 127) / 128;
-      // one thread per (row, half): half 0 writes the message chunks, half 1 the self chunks
-      for (int idx = u.tid; idx < 2 * R; idx += u.nthr) {
-        const int q = idx >> 1, v = r0 + q;
-        if ((idx & 1) == 0) {
-          const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
-          for (int ch = 0; ch < F8; ++ch) {
-            float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
-            uint4 w;
-            w.x = pack_bf16(acc[0], acc[1]);
-            w.y = pack_bf16(acc[2], acc[3]);
-            w.z = pack_bf16(acc[4], acc[5]);
-            w.w = pack_bf16(acc[6], acc[7]);
-            *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
-          }
-        } else {
-          for (int ch = 0; ch < F8; ++ch)
-            *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
-                *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
-        }
+      // one thread per (row, 8-feature chunk): the message chunk and the self chunk
+      for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
+        const int q = idx / F8, ch = idx - q * F8, v = r0 + q;
+        const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
+        uint4 w;
+        w.x = pack_bf16(acc[0], acc[1]);
+        w.y = pack_bf16(acc[2], acc[3]);
+        w.z = pack_bf16(acc[4], acc[5]);
+        w.w = pack_bf16(acc[6], acc[7]);
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
+            *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
       }
       if (!run_mmas(c, u, nt)) return false;
       epilogue_fwd(c, u, nt, R, r0, l, c.a->op == TC_ELOC);
@@ -483,7 +483,8 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
 
 // dX rows of a bond group at layer l, gathered into the unit's A tiles:
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
-// One thread per (row, half): half 0 writes the message chunks, half 1 the self chunks.
+// One thread per (row, 8-feature chunk): the chunk of the message and the chunk of the self
+// term, so that every thread of the unit does the same amount of work.
 __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, G = c.G, ldh = c.ldh;
@@ -492,60 +493,29 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
   const int* offl = u.soff + l * (G + 1);
   const int R = offl[nb];
   const __nv_bfloat16* dp = new16(c, u, l - 1);
-  for (int idx = u.tid; idx < 2 * R; idx += u.nthr) {
-    const int q = idx >> 1;
+  for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
+    const int q = idx / F8, ch = idx - q * F8;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
-    const int e = u.slot_e[k];
-    const int bo = __ldg(g.ball_off + e);
+    const int bo = __ldg(g.ball_off + u.slot_e[k]);
     const int sprev = offp[k + 1] - offp[k];
-    const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh;
-    if ((idx & 1) == 0) {
-      const int v = __ldg(g.ball_vert + bo + r);
-      const int nb0 = __ldg(g.row_nbr + bo + r);
-      const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
-      // the neighbours inside ball_{l-1} (the only nonzero dH^{l-1} rows), loaded once
-      const int dg = k1 - k0;
-      int pp[8];
-      float ww[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        pp[t] = -1;
-        ww[t] = 0.f;
-        if (t < dg) {
-          const int p = __ldg(g.nbr_pos + nb0 + t);
-          if (p < sprev) {
-            pp[t] = p;
-            ww[t] = __ldg(g.wf + k0 + t);
-          }
-        }
-      }
-      for (int ch = 0; ch < F8; ++ch) {
-        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (dg <= 8) {
-#pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (pp[t] >= 0) fma_chunk(acc, ww[t], drow + (size_t)pp[t] * ldh + ch * 8);
-        } else {
-          for (int kk = k0; kk < k1; ++kk) {
-            const int p = __ldg(g.nbr_pos + nb0 + (kk - k0));
-            if (p < sprev) fma_chunk(acc, __ldg(g.wf + kk), drow + (size_t)p * ldh + ch * 8);
-          }
-        }
-        uint4 w;
-        w.x = pack_bf16(acc[0], acc[1]);
-        w.y = pack_bf16(acc[2], acc[3]);
-        w.z = pack_bf16(acc[4], acc[5]);
-        w.w = pack_bf16(acc[6], acc[7]);
-        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
-      }
-    } else {
-      for (int ch = 0; ch < F8; ++ch) {
-        const uint4 w = r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh + ch * 8)
-                                  : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) = w;
-      }
+    const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh + ch * 8;
+    const int v = __ldg(g.ball_vert + bo + r);
+    const int* np = g.nbr_pos + __ldg(g.row_nbr + bo + r);
+    const int k0 = __ldg(g.row_ptr + v), dg = __ldg(g.row_ptr + v + 1) - k0;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < dg; ++t) {
+      const int p = __ldg(np + t);
+      if (p < sprev) fma_chunk(acc, __ldg(g.wf + k0 + t), drow + (size_t)p * ldh);
     }
+    uint4 w;
+    w.x = pack_bf16(acc[0], acc[1]);
+    w.y = pack_bf16(acc[2], acc[3]);
+    w.z = pack_bf16(acc[4], acc[5]);
+    w.w = pack_bf16(acc[6], acc[7]);
+    *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
+    *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
+        r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh) : make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -679,7 +649,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_fail;
   __shared__ int s_count;
-  __shared__ double s_eu[2 * kTcUnits];
+  __shared__ double s_eu[2 * kTcMaxUnits];
   TcCtx c;
   c.a = &a;
   c.N = a.m.N;
@@ -708,7 +678,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int h = 0; h < kTcUnits; ++h) mbar_init(bars + h, 1);
+    for (int h = 0; h < a.lay.units; ++h) mbar_init(bars + h, 1);
   }
   if ((threadIdx.x >> 5) == 0) {
     tmem_alloc(slot, kTmemCols);
@@ -740,12 +710,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   whole.tbase = tmem;
   whole.bar = bars;
   whole.phase = 0;
-  const int h = threadIdx.x / kTcUnitThreads;
+  const int U = a.lay.units, unit_threads = kTcThreads / U;
+  const int h = threadIdx.x / unit_threads;
   Unit u;
-  u.tid = threadIdx.x % kTcUnitThreads;
-  u.nthr = kTcUnitThreads;
+  u.tid = threadIdx.x % unit_threads;
+  u.nthr = unit_threads;
   u.bar_id = 1 + h;
-  u.nwg = kTcUnitThreads / 128;
+  u.nwg = unit_threads / 128;
   u.A = smem + a.lay.oA + (size_t)h * a.lay.a_unit;
   u.tbase = tmem + (uint32_t)(h * c.T * F);
   u.bar = bars + h;
@@ -803,9 +774,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       for (int e = threadIdx.x; e < c.E; e += blockDim.x) a.dlogpsi[b * c.E + e] = 0.f;
     __syncthreads();
     const int na = s_count;
-    // unit h takes the bond groups h, h + kTcUnits, ...
+    // unit h takes the bond groups h, h + U, ...
     double er = 0.0, ei = 0.0;
-    for (int t0 = h * c.G; t0 < na; t0 += kTcUnits * c.G) {
+    for (int t0 = h * c.G; t0 < na; t0 += U * c.G) {
       const int nb = min(c.G, na - t0);
       if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
       unit_sync(u);
@@ -833,7 +804,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     ok = s_fail == 0;
     if (threadIdx.x == 0 && ok) {
       double re = diag, im = 0.0;
-      for (int hh = 0; hh < kTcUnits; ++hh) {
+      for (int hh = 0; hh < U; ++hh) {
         re += s_eu[2 * hh];
         im += s_eu[2 * hh + 1];
       }
@@ -844,6 +815,575 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   }
   // teardown: on failure wait (bounded) for the MMAs in flight before freeing TMEM
   if (!ok && u.tid == 0) mbar_wait_bounded(u.bar, u.phase ^ 1u);  // the phase that timed out
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------------
+// Metropolis pair-exchange sweeps on the tensor cores (plain moves, BF16 models)
+// ---------------------------------------------------------------------------------
+// The move rule is the one of the CUDA-core samplers: step t of chain c draws
+// Philox4x64-10(key = (seed, c), counter = (t, 0, 0, 0)), bond e = hi64(r0 |E|), a
+// parallel bond is a rejected no-op, an antiparallel one is accepted iff
+// (r1 >> 40) 2^-24 < exp(2 Re Delta).  Delta is the difference propagation of the local
+// energy kernel (BF16 operands on the tensor cores, FP32 accumulation and activations).
+//
+// Each unit owns a pool of G chains.  In one round every unfinished chain of the pool
+// first runs through its no-op steps (a thread per chain), stopping at its next
+// antiparallel proposal (or at a sweep whose sample is recorded); the pending proposals
+// of the pool are then evaluated together as one bond group -- the rows of all of them
+// share the A tiles of each layer -- and accepted or rejected independently.  Chains are
+// independent, so this schedule changes nothing in any chain's trajectory.
+//
+// Per chain, the unit keeps in the workspace (L2-resident: a few hundred KiB per SM) the
+// FP32 pre-activations Y^1..Y^L of the current configuration and the dY rows of the
+// pending proposal; an accepted move adds dY to Y.  The chain's Y is computed by a
+// tensor-core forward when the chain enters the pool.
+struct TcmArgs {
+  TcArgs base;  // graph, dims, theta and the layout of the A tiles / dH rows / partials
+  int8_t* chain_spins;
+  int64_t C;
+  int n_sweeps, record_every;
+  uint64_t seed, step0;
+  int8_t* samples_out;
+  double* logpsi_out;
+  int32_t* n_acc;
+  double* trace;
+  float* gws;                  // per unit: G slots of slot_elems, then the H scratch
+  uint64_t slot_elems;         // Y^1..Y^L [L][N][F], then dY rows (FP32 elements)
+  uint64_t unit_elems;         // FP32 elements per unit (slots + two BF16 H layers)
+  uint64_t dy_off[kMaxL + 1];  // element offset of the dY^l rows in a slot (l = 1..L)
+};
+
+struct TcmSlots {        // per-unit pool state (shared memory)
+  int64_t* chain;        // [G] chain index or -1
+  int64_t* step;         // [G] steps done in this launch
+  int64_t* wbase;        // [G] first step of the cached Philox words
+  uint64_t* words;       // [G][32][2] (r0, r1) of steps wbase .. wbase + 31
+  uint64_t* r1;          // [G] uniform word of the pending proposal
+  double* red;           // [2 * unit threads] reduction scratch
+  int* flag;             // [G] bit 0: proposal pending, bit 1: record pending, bit 2: done
+  int* acc;              // [G] accepted moves in this launch
+  int* bond;             // [G] bond of the pending proposal
+  int* gslot;            // [G] slot of group member k
+  int* ok;               // [G] group member k accepted
+  int8_t* spins;         // [G][N]
+};
+
+__host__ __device__ inline size_t tcm_state_bytes(int G, int N, int unit_threads) {
+  const size_t b = (size_t)G * 8 * 4 + (size_t)G * 32 * 16 + (size_t)unit_threads * 16 + (size_t)G * 4 * 5 + (size_t)G * N;
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ float* tcm_slot(const TcmArgs& a, int unit_global, int s) {
+  return a.gws + (size_t)unit_global * a.unit_elems + (size_t)s * a.slot_elems;
+}
+
+// Forward of slot s's configuration: fills its Y^1..Y^L (FP32) through the unit's tiles.
+__device__ bool tcm_forward(const TcCtx& c, Unit& u, const TcmArgs& a, float* Ys, __nv_bfloat16* Hs,
+                            const int8_t* sp) {
+  const int N = c.N, F = c.F, L = c.L, ldh = c.ldh, F8 = F / 8;
+  const DevGraph& g = c.a->g;
+  for (int i = u.tid; i < N * F; i += u.nthr)
+    Hs[(size_t)(i / F) * ldh + i % F] = __float2bfloat16_rn(c.emb[(sp[i / F] > 0 ? 0 : 1) * F + i % F]);
+  unit_sync(u);
+  const int rows_per_pass = c.T * 128;
+  const int warp = u.tid >> 5, lane = u.tid & 31, q4 = warp & 3, wg = warp >> 2;
+  for (int l = 1; l <= L; ++l) {
+    const __nv_bfloat16* hp = Hs + (size_t)((l - 1) & 1) * N * ldh;
+    __nv_bfloat16* hn = Hs + (size_t)(l & 1) * N * ldh;
+    float* Y = Ys + (size_t)(l - 1) * N * F;
+    for (int r0 = 0; r0 < N; r0 += rows_per_pass) {
+      const int R = min(rows_per_pass, N - r0);
+      const int nt = (R + 127) / 128;
+      for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
+        const int q = idx / F8, ch = idx - q * F8, v = r0 + q;
+        const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
+        uint4 w;
+        w.x = pack_bf16(acc[0], acc[1]);
+        w.y = pack_bf16(acc[2], acc[3]);
+        w.z = pack_bf16(acc[4], acc[5]);
+        w.w = pack_bf16(acc[6], acc[7]);
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
+            *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
+      }
+      if (!run_mmas(c, u, nt)) return false;
+      for (int t = 0; t < nt; ++t) {
+        const int q = t * 128 + q4 * 32 + lane;
+        for (int ch = wg; ch < F8; ch += u.nwg) {
+          float v8[8];
+          tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + ch * 8), v8);
+          if (q < R) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v8[i] += c.bias[ch * 8 + i];
+            float4* yo = reinterpret_cast<float4*>(Y + (size_t)(r0 + q) * F + ch * 8);
+            yo[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
+            yo[1] = make_float4(v8[4], v8[5], v8[6], v8[7]);
+            if (l < L) {
+              uint4 w;
+              w.x = pack_bf16(tanh_fast(v8[0]), tanh_fast(v8[1]));
+              w.y = pack_bf16(tanh_fast(v8[2]), tanh_fast(v8[3]));
+              w.z = pack_bf16(tanh_fast(v8[4]), tanh_fast(v8[5]));
+              w.w = pack_bf16(tanh_fast(v8[6]), tanh_fast(v8[7]));
+              *reinterpret_cast<uint4*>(hn + (size_t)(r0 + q) * ldh + ch * 8) = w;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      unit_sync(u);
+    }
+  }
+  return true;
+}
+
+// dY in TMEM -> dH for the group rows at layer l; the chains' own Y^l rows are read from
+// their slots, dY^l rows are kept in the slots for the update on acceptance.
+__device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int l,
+                             int nt, int nb) {
+  const DevGraph& g = c.a->g;
+  const int warp = u.tid >> 5, lane = u.tid & 31;
+  const int q4 = warp & 3, wg = warp >> 2;
+  const int F = c.F, L = c.L, N = c.N, G = c.G, ldh = c.ldh;
+  const int* offl = u.soff + l * (G + 1);
+  const int R = offl[nb];
+  __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
+  for (int t = 0; t < nt; ++t) {
+    const int q = t * 128 + q4 * 32 + lane;
+    const float* yrow = nullptr;
+    float* dyrow = nullptr;
+    if (q < R) {
+      const int k = slot_of(offl, nb, q);
+      const int r = q - offl[k];
+      const int v = __ldg(g.ball_vert + __ldg(g.ball_off + u.slot_e[k]) + r);
+      float* sl = tcm_slot(a, ug, S.gslot[k]);
+      yrow = sl + (size_t)(l - 1) * N * F + (size_t)v * F;
+      dyrow = sl + a.dy_off[l] + (size_t)r * F;
+    }
+    float pre = 0.f, pim = 0.f;
+    for (int ch = wg; ch < F / 8; ch += u.nwg) {
+      const int col = ch * 8;
+      float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
+      if (q < R) {
+        y0 = *reinterpret_cast<const float4*>(yrow + col);
+        y1 = *reinterpret_cast<const float4*>(yrow + col + 4);
+      }
+      float dy[8];
+      tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
+      if (q < R) {
+        reinterpret_cast<float4*>(dyrow + col)[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
+        reinterpret_cast<float4*>(dyrow + col)[1] = make_float4(dy[4], dy[5], dy[6], dy[7]);
+        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+        float d[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float e = __expf(-2.f * fabsf(yv[i]));
+          const float sg = yv[i] < 0.f ? -1.f : 1.f;
+          const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
+          const float ope = 1.f + e;
+          const float den = ope * (ope + sg * (1.f - e) * tt);
+          d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(yv[i] + dy[i]) - tanhf(yv[i]);
+        }
+        if (l < L) {
+          uint4 w;
+          w.x = pack_bf16(d[0], d[1]);
+          w.y = pack_bf16(d[2], d[3]);
+          w.z = pack_bf16(d[4], d[5]);
+          w.w = pack_bf16(d[6], d[7]);
+          *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            pre += d[i] * c.wr[2 * (col + i)];
+            pim += d[i] * c.wr[2 * (col + i) + 1];
+          }
+        }
+      }
+    }
+    if (l == L && q < R) {
+      u.part[((size_t)wg * c.T * 128 + q) * 2] = pre;
+      u.part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
+    }
+  }
+  tc_fence_before();
+  unit_sync(u);
+}
+
+// Delta log Psi of the pending proposals of group members 0..nb-1 (bonds u.slot_e).
+__device__ bool tcm_group(const TcCtx& c, Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int nb) {
+  const DevGraph& g = c.a->g;
+  const int F = c.F, L = c.L, G = c.G, Lm = g.Lmax;
+  if (u.tid == 0) {
+    for (int l = 0; l <= L; ++l) {
+      int o = 0;
+      for (int k = 0; k < nb; ++k) {
+        u.soff[l * (G + 1) + k] = o;
+        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
+      }
+      u.soff[l * (G + 1) + nb] = o;
+    }
+  }
+  unit_sync(u);
+  __nv_bfloat16* d0 = new16(c, u, 0);
+  for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
+    const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
+    const int e = u.slot_e[k];
+    const int8_t* sp = S.spins + (size_t)S.gslot[k] * c.N;
+    const int self = __ldg(g.edges + 2 * e + r), other = __ldg(g.edges + 2 * e + (1 - r));
+    const float dv = c.emb[(sp[other] > 0 ? 0 : 1) * F + f] - c.emb[(sp[self] > 0 ? 0 : 1) * F + f];
+    d0[(size_t)(u.soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
+  }
+  unit_sync(u);
+  for (int l = 1; l <= L; ++l) {
+    gather_delta(c, u, l, nb);
+    const int nt = (u.soff[l * (G + 1) + nb] + 127) / 128;
+    if (!run_mmas(c, u, nt)) return false;
+    tcm_epilogue(c, u, a, S, ug, l, nt, nb);
+  }
+  const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
+  const int* offL = u.soff + L * (G + 1);
+  const size_t wgs = (size_t)c.T * 128;
+  for (int k = warp; k < nb; k += nwarps) {
+    float dre = 0.f, dim = 0.f;
+    for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
+      for (int w = 0; w < min(u.nwg, F / 8); ++w) {
+        dre += u.part[(w * wgs + q) * 2];
+        dim += u.part[(w * wgs + q) * 2 + 1];
+      }
+    }
+    dre = warp_sum_t(dre);
+    dim = warp_sum_t(dim);
+    if (lane == 0) {
+      u.res[2 * k] = (double)dre;
+      u.res[2 * k + 1] = (double)dim;
+    }
+  }
+  unit_sync(u);
+  return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_fail;
+  __shared__ int s_more[kTcMaxUnits];
+  const TcArgs& b = a.base;
+  TcCtx c;
+  c.a = &b;
+  c.N = b.m.N;
+  c.F = b.m.F;
+  c.L = b.m.L;
+  c.E = b.m.E;
+  c.T = b.lay.T;
+  c.G = b.lay.G;
+  c.ldh = b.m.F + 8;
+  c.ldy = b.m.F + 4;
+  c.Wt = (__nv_bfloat16*)(smem + b.lay.oWt);
+  c.bias = (float*)(smem + b.lay.obias);
+  c.emb = (float*)(smem + b.lay.oemb);
+  c.wr = (float*)(smem + b.lay.owr);
+  c.br = (float*)(smem + b.lay.obr);
+  c.spin = nullptr;
+  c.list = (int*)(smem + b.lay.oint);
+  c.sdbl = (double*)(smem + b.lay.odbl);
+  c.region = smem + b.lay.oregion;
+  c.fail = &s_fail;
+  const int F = c.F, N = c.N, L = c.L, G = c.G, E = c.E;
+  const Dims& m = b.m;
+  const float* th = b.theta;
+  uint64_t* bars = (uint64_t*)(smem + b.lay.obar);
+  uint32_t* slot = (uint32_t*)(smem + b.lay.oslot);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int h = 0; h < b.lay.units; ++h) mbar_init(bars + h, 1);
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    tmem_alloc(slot, kTmemCols);
+    tmem_relinquish();
+  }
+  const float* W = th + m.oW;
+  for (int i = threadIdx.x; i < F * 2 * F; i += blockDim.x) {
+    const int n = i / (2 * F), k = i % (2 * F);
+    unsigned char* p = (unsigned char*)c.Wt + (size_t)(n >> 3) * (32 * F) + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+  }
+  for (int i = threadIdx.x; i < F; i += blockDim.x) c.bias[i] = th[m.ob + i];
+  for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
+  for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) c.wr[i] = th[m.owr + i];
+  if (threadIdx.x < 2) c.br[threadIdx.x] = th[m.obr + threadIdx.x];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  const int U = b.lay.units, unit_threads = kTcThreads / U;
+  const int h = threadIdx.x / unit_threads;
+  Unit u;
+  u.tid = threadIdx.x % unit_threads;
+  u.nthr = unit_threads;
+  u.bar_id = 1 + h;
+  u.nwg = unit_threads / 128;
+  u.A = smem + b.lay.oA + (size_t)h * b.lay.a_unit;
+  u.tbase = tmem + (uint32_t)(h * c.T * F);
+  u.bar = bars + h;
+  u.phase = 0;
+  u.d16 = (__nv_bfloat16*)(c.region + b.lay.rnew16 + (size_t)h * b.lay.new16_unit);
+  u.part = (float*)(c.region + b.lay.rpart + (size_t)h * b.lay.part_unit);
+  u.slot_e = c.list + h * b.lay.int_unit;
+  u.soff = u.slot_e + G;
+  u.res = c.sdbl + h * b.lay.dbl_unit;
+  // pool state of this unit: after the unit's ints and doubles
+  TcmSlots S;
+  {
+    unsigned char* st = c.region + b.lay.rstate + (size_t)h * b.lay.state_unit;
+    S.chain = (int64_t*)st;
+    S.step = S.chain + G;
+    S.wbase = S.step + G;
+    S.r1 = (uint64_t*)(S.wbase + G);
+    S.words = S.r1 + G;
+    S.red = (double*)(S.words + (size_t)G * 64);
+    S.flag = (int*)(S.red + 2 * unit_threads);
+    S.acc = S.flag + G;
+    S.bond = S.acc + G;
+    S.gslot = S.bond + G;
+    S.ok = S.gslot + G;
+    S.spins = (int8_t*)(S.ok + G);
+  }
+  const int ug = blockIdx.x * U + h;                 // this unit's workspace index
+  float* Hs_f = a.gws + (size_t)ug * a.unit_elems + (size_t)G * a.slot_elems;
+  __nv_bfloat16* Hs = (__nv_bfloat16*)Hs_f;
+  const int64_t n_steps = (int64_t)a.n_sweeps * N;
+  const int64_t pools = (a.C + G - 1) / G;
+
+  bool ok = true;
+  for (int64_t pool = (int64_t)blockIdx.x * U + h; pool < pools && ok; pool += (int64_t)gridDim.x * U) {
+    // enter the pool's chains
+    for (int s = 0; s < G; ++s) {
+      const int64_t ch = pool * G + s;
+      for (int v = u.tid; v < N; v += u.nthr) S.spins[(size_t)s * N + v] = ch < a.C ? a.chain_spins[ch * N + v] : (int8_t)1;
+      if (u.tid == 0) {
+        S.chain[s] = ch < a.C ? ch : -1;
+        S.step[s] = 0;
+        S.wbase[s] = -64;
+        S.flag[s] = ch < a.C ? 0 : 4;
+        S.acc[s] = 0;
+      }
+    }
+    unit_sync(u);
+    for (int s = 0; s < G && ok; ++s) {
+      if (S.chain[s] < 0) continue;
+      ok = tcm_forward(c, u, a, tcm_slot(a, ug, s), Hs, S.spins + (size_t)s * N);
+    }
+    if (!ok) break;
+    while (true) {
+      // 1. each chain runs through its no-op steps up to its next proposal or record (one
+      //    warp per chain: its lanes draw the Philox words of 32 steps at once)
+      {
+        const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
+        for (int s = warp; s < G; s += nwarps) {
+          int fl = S.flag[s] & 4;
+          if (fl) continue;
+          const int64_t ch = S.chain[s];
+          const int8_t* sp = S.spins + (size_t)s * N;
+          int64_t k = S.step[s];
+          if (k >= n_steps) fl = 4;
+          while (!fl) {
+            if (k >= S.wbase[s] + 32) {
+              __syncwarp();
+              const U64x4 w = philox4x64_10(a.seed, (uint64_t)ch, U64x4{a.step0 + (uint64_t)(k + lane), 0, 0, 0});
+              S.words[((size_t)s * 32 + lane) * 2] = w.x;
+              S.words[((size_t)s * 32 + lane) * 2 + 1] = w.y;
+              __syncwarp();
+              if (lane == 0) S.wbase[s] = k;
+              __syncwarp();
+            }
+            // lane 0 scans the cached steps; the outcome is broadcast
+            int stop = 0, eb = 0;
+            int64_t kn = k;
+            if (lane == 0) {
+              const int64_t wb = S.wbase[s];
+              while (kn < wb + 32 && kn < n_steps) {
+                const uint64_t r0 = S.words[((size_t)s * 32 + (kn - wb)) * 2];
+                const int e = (int)__umul64hi(r0, (uint64_t)E);
+                if (sp[__ldg(b.g.edges + 2 * e)] != sp[__ldg(b.g.edges + 2 * e + 1)]) {
+                  S.r1[s] = S.words[((size_t)s * 32 + (kn - wb)) * 2 + 1];
+                  eb = e;
+                  stop = 1;
+                  break;
+                }
+                if (a.trace) {
+                  double* tr = a.trace + ((size_t)ch * n_steps + kn) * 4;
+                  tr[0] = (double)e;
+                  tr[1] = 0.0;
+                  tr[2] = __longlong_as_double(0x7ff8000000000000ll);
+                  tr[3] = 1.0;
+                }
+                ++kn;
+                if (a.record_every > 0 && kn % N == 0 && (kn / N) % a.record_every == 0) {
+                  stop = 2;
+                  break;
+                }
+                if (kn >= n_steps) {
+                  stop = 4;
+                  break;
+                }
+              }
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            k = __shfl_sync(0xffffffffu, kn, 0);
+            eb = __shfl_sync(0xffffffffu, eb, 0);
+            if (stop) {
+              fl = stop;
+              if (lane == 0 && stop == 1) S.bond[s] = eb;
+            }
+          }
+          if (lane == 0) {
+            S.step[s] = k;
+            S.flag[s] = fl;
+          }
+        }
+      }
+      unit_sync(u);
+      // 2. the pending proposals as one group
+      if (u.tid == 0) {
+        int nb = 0, more = 0;
+        for (int s = 0; s < G; ++s) {
+          if (S.flag[s] & 1) {
+            S.gslot[nb] = s;
+            u.slot_e[nb] = S.bond[s];
+            ++nb;
+          }
+          if (!(S.flag[s] & 4)) more = 1;
+        }
+        u.soff[(L + 1) * (G + 1)] = nb;  // spare slot after the offsets
+        s_more[h] = more;
+      }
+      unit_sync(u);
+      const int nb = u.soff[(L + 1) * (G + 1)];
+      if (nb > 0) {
+        if (!tcm_group(c, u, a, S, ug, nb)) {
+          ok = false;
+          break;
+        }
+        // 3. decisions
+        if (u.tid < nb) {
+          const int k = u.tid, s = S.gslot[k];
+          const float dre = (float)u.res[2 * k];
+          const bool acc = (float)(S.r1[s] >> 40) * 0x1.0p-24f < expf(2.0f * dre);
+          S.ok[k] = acc ? 1 : 0;
+          if (acc) ++S.acc[s];
+          if (a.trace) {
+            double* tr = a.trace + ((size_t)S.chain[s] * n_steps + S.step[s]) * 4;
+            tr[0] = (double)u.slot_e[k];
+            tr[1] = acc ? 1.0 : 0.0;
+            tr[2] = (double)dre;
+            tr[3] = 1.0;
+          }
+        }
+        unit_sync(u);
+        // 4. accepted moves: Y += dY on the bond's balls, exchange the spins
+        for (int k = 0; k < nb; ++k) {
+          if (!S.ok[k]) continue;
+          const int s = S.gslot[k], e = u.slot_e[k];
+          float* sl = tcm_slot(a, ug, s);
+          const int bo = __ldg(b.g.ball_off + e);
+          for (int l = 1; l <= L; ++l) {
+            const int R = __ldg(b.g.ball_size + (size_t)e * (b.g.Lmax + 1) + l);
+            float* Y = sl + (size_t)(l - 1) * N * F;
+            const float* dY = sl + a.dy_off[l];
+            for (int i = u.tid; i < R * (F / 4); i += u.nthr) {
+              const int r = i / (F / 4), f4 = i - r * (F / 4);
+              const int v = __ldg(b.g.ball_vert + bo + r);
+              float4* y = reinterpret_cast<float4*>(Y + (size_t)v * F) + f4;
+              const float4 d = reinterpret_cast<const float4*>(dY + (size_t)r * F)[f4];
+              float4 t = *y;
+              t.x += d.x;
+              t.y += d.y;
+              t.z += d.z;
+              t.w += d.w;
+              *y = t;
+            }
+          }
+          if (u.tid == 0) {
+            int8_t* sp = S.spins + (size_t)s * N;
+            const int i = __ldg(b.g.edges + 2 * e), j = __ldg(b.g.edges + 2 * e + 1);
+            const int8_t t = sp[i];
+            sp[i] = sp[j];
+            sp[j] = t;
+          }
+        }
+        unit_sync(u);
+        if (u.tid < G && (S.flag[u.tid] & 1)) {
+          const int s = u.tid;
+          const int64_t k = ++S.step[s];
+          int fl = k >= n_steps ? 4 : 0;
+          if (a.record_every > 0 && k % N == 0 && (k / N) % a.record_every == 0) fl = 2;
+          S.flag[s] = fl;
+        }
+        unit_sync(u);
+      }
+      // 5. samples of the chains that completed a recorded sweep
+      for (int s = 0; s < G; ++s) {
+        if (!(S.flag[s] & 2)) continue;
+        const int64_t ch = S.chain[s];
+        const int rec = (int)(S.step[s] / N) / a.record_every - 1;
+        const int8_t* sp = S.spins + (size_t)s * N;
+        if (a.samples_out)
+          for (int v = u.tid; v < N; v += u.nthr) a.samples_out[((size_t)rec * a.C + ch) * N + v] = sp[v];
+        if (a.logpsi_out) {
+          const float* YL = tcm_slot(a, ug, s) + (size_t)(L - 1) * N * F;
+          float re = 0.f, im = 0.f;
+          for (int i = u.tid; i < N * F; i += u.nthr) {
+            const float hv = tanhf(YL[i]);
+            const int f = i % F;
+            re += hv * c.wr[2 * f];
+            im += hv * c.wr[2 * f + 1];
+          }
+          S.red[2 * u.tid] = (double)re;
+          S.red[2 * u.tid + 1] = (double)im;
+          unit_sync(u);
+          if (u.tid == 0) {
+            double zr = 0.0, zi = 0.0;
+            for (int t = 0; t < u.nthr; ++t) {
+              zr += S.red[2 * t];
+              zi += S.red[2 * t + 1];
+            }
+            int up = 0;
+            for (int v = 0; v < N; ++v) up += sp[v] > 0;
+            const int dn = N - up;
+            a.logpsi_out[((size_t)rec * a.C + ch) * 2] =
+                zr + (double)up * c.wr[2 * F] + (double)dn * c.wr[2 * (F + 1)] + (double)c.br[0];
+            a.logpsi_out[((size_t)rec * a.C + ch) * 2 + 1] =
+                zi + (double)up * c.wr[2 * F + 1] + (double)dn * c.wr[2 * (F + 1) + 1] + (double)c.br[1];
+          }
+        }
+        unit_sync(u);
+        if (u.tid == 0) S.flag[s] = S.step[s] >= n_steps ? 4 : 0;
+        unit_sync(u);
+      }
+      if (!s_more[h]) break;
+    }
+    if (!ok) break;
+    // leave the pool: configurations and acceptance counts back
+    for (int s = 0; s < G; ++s) {
+      const int64_t ch = S.chain[s];
+      if (ch < 0) continue;
+      for (int v = u.tid; v < N; v += u.nthr) a.chain_spins[ch * N + v] = S.spins[(size_t)s * N + v];
+      if (u.tid == 0 && a.n_acc) a.n_acc[ch] += S.acc[s];
+    }
+    unit_sync(u);
+  }
+  if (!ok) {
+    if (u.tid == 0) {
+      atomicOr(&s_tc_status, 1);
+      mbar_wait_bounded(u.bar, u.phase ^ 1u);
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -868,7 +1408,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
   const int T = tc_tiles_per_unit(m.F);
-  if (kTcUnits * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
+  if (tc_units(m.F) * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   const size_t budget = (size_t)di.smem_optin - 2048;
   int G = op == TC_ELOC ? (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1) : 1;
   if (G > 16) G = 16;
@@ -941,6 +1481,159 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   a.gregion = (unsigned char*)ws;
   a.region_in_smem = p.region_in_smem;
   k_tc<<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// host: tensor-core sampler
+// ---------------------------------------------------------------------------------
+struct TcmPlan {
+  TcLayout lay;
+  int grid = 0;
+  uint64_t slot_elems = 0, unit_elems = 0;
+  uint64_t dy_off[kMaxL + 1] = {0};
+  size_t ws_bytes = 0;
+};
+
+static void tcm_layout(const Dims& m, const int* maxball, int G, TcLayout* t) {
+  const int F = m.F, N = m.N, L = m.L;
+  memset(t, 0, sizeof(*t));
+  uint64_t o = 0;
+  auto take = [&](uint64_t bytes, uint64_t align) {
+    o = (o + align - 1) / align * align;
+    uint64_t r = o;
+    o += bytes;
+    return (uint32_t)r;
+  };
+  t->T = tc_tiles_per_unit(F);
+  t->units = tc_units(F);
+  const int U = t->units, unit_threads = kTcThreads / U;
+  t->G = G;
+  t->a_unit = (uint32_t)t->T * 128 * 2 * F * 2;
+  t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
+  t->oA = take((uint64_t)U * t->a_unit, 1024);
+  t->obias = take(F * 4, 16);
+  t->oemb = take(2 * F * 4, 16);
+  t->owr = take((F + 2) * 2 * 4, 16);
+  t->obr = take(16, 16);
+  t->int_unit = (uint32_t)(G + (L + 1) * (G + 1) + 4);
+  t->oint = take((uint64_t)U * t->int_unit * 4, 16);
+  t->dbl_unit = (uint32_t)(2 * G + 4);
+  t->odbl = take((uint64_t)U * t->dbl_unit * 8, 16);
+  t->obar = take(8 * U, 8);
+  t->oslot = take(4, 4);
+  uint64_t r = 0;
+  auto rtake = [&](uint64_t bytes) {
+    r = (r + 15) / 16 * 16;
+    uint64_t x = r;
+    r += bytes;
+    return x;
+  };
+  const uint64_t ldh = F + 8;
+  uint64_t n16 = 0;
+  for (int l = 0; l < L; ++l) {
+    t->new16_off[l] = n16;
+    n16 += (uint64_t)G * maxball[l] * ldh * 2;
+  }
+  t->new16_unit = (n16 + 15) / 16 * 16;
+  t->rnew16 = rtake((uint64_t)U * t->new16_unit);
+  t->part_unit = (uint64_t)(unit_threads / 128) * t->T * 128 * 2 * 4;
+  t->rpart = rtake((uint64_t)U * t->part_unit);
+  t->state_unit = tcm_state_bytes(G, N, unit_threads);
+  t->rstate = rtake((uint64_t)U * t->state_unit);
+  t->region_bytes = (r + 255) / 256 * 256;
+  t->oregion = take(t->region_bytes, 16);
+  t->smem_total = (uint32_t)o;
+}
+
+static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan* p, int* maxball) {
+  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared) return GNA_ERR_UNSUPPORTED;
+  DeviceInfo di;
+  gna_status st = device_info(&di);
+  if (st != GNA_OK) return st;
+  if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
+  for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
+  const int T = tc_tiles_per_unit(m.F), U = tc_units(m.F);
+  if (U * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
+  int G = (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1);
+  if (G > 16) G = 16;
+  if (G < 1) return GNA_ERR_UNSUPPORTED;
+  const size_t budget = (size_t)di.smem_optin - 2048;
+  TcLayout lay;
+  for (; G >= 1; --G) {
+    tcm_layout(m, maxball, G, &lay);
+    if (lay.smem_total <= budget) break;
+  }
+  if (G < 1) return GNA_ERR_UNSUPPORTED;
+  const uint32_t min_smem = (uint32_t)(228u * 1024u / (512 / kTmemCols + 1)) + 1024u;
+  if (lay.smem_total < min_smem) lay.smem_total = min_smem;
+  p->lay = lay;
+  GNA_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_metro, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)lay.smem_total));
+  int occ = 0;
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_tc_metro, kTcThreads, lay.smem_total));
+  if (occ < 1) occ = 1;
+  if (occ * kTmemCols > 512) return GNA_ERR_UNSUPPORTED;
+  const int64_t pools = (C + G - 1) / G;
+  int64_t grid = (int64_t)di.sms * occ;
+  if (grid * U > pools) grid = (pools + U - 1) / U;
+  if (grid < 1) grid = 1;
+  p->grid = (int)grid;
+  const uint64_t NF = (uint64_t)m.N * m.F;
+  uint64_t e = (uint64_t)m.L * NF;
+  for (int l = 1; l <= m.L; ++l) {
+    p->dy_off[l] = e;
+    e += (uint64_t)maxball[l] * m.F;
+  }
+  p->slot_elems = (e + 3) / 4 * 4;
+  p->unit_elems = (uint64_t)G * p->slot_elems + (uint64_t)m.N * (m.F + 8);  // + two BF16 H layers
+  p->ws_bytes = align_up((size_t)grid * U * p->unit_elems * sizeof(float));
+  return GNA_OK;
+}
+
+gna_status tcm_workspace(const gna_graph* g, const Dims& m, int64_t C, size_t* bytes) {
+  if (C == 0) {
+    *bytes = 0;
+    return GNA_OK;
+  }
+  TcmPlan p;
+  int maxball[kMaxL + 1];
+  gna_status st = tcm_plan(g, m, C, &p, maxball);
+  if (st != GNA_OK) return st;
+  *bytes = p.ws_bytes;
+  return GNA_OK;
+}
+
+gna_status tcm_run(const TcmCall& call, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (call.C == 0 || call.n_sweeps == 0) return GNA_OK;
+  TcmPlan p;
+  TcmArgs a;
+  memset(&a, 0, sizeof(a));
+  gna_status st = tcm_plan(call.g, call.m, call.C, &p, a.base.maxball);
+  if (st != GNA_OK) return st;
+  if (ws_bytes < p.ws_bytes || !ws) return GNA_ERR_WORKSPACE;
+  a.base.g = call.g->d;
+  a.base.m = call.m;
+  a.base.op = TC_ELOC;
+  a.base.lay = p.lay;
+  a.base.theta = call.theta;
+  a.base.region_in_smem = 1;
+  a.chain_spins = call.chain_spins;
+  a.C = call.C;
+  a.n_sweeps = call.n_sweeps;
+  a.record_every = call.record_every;
+  a.seed = call.seed;
+  a.step0 = call.step0;
+  a.samples_out = call.samples_out;
+  a.logpsi_out = call.logpsi_out;
+  a.n_acc = call.n_acc;
+  a.trace = call.trace;
+  a.gws = (float*)ws;
+  a.slot_elems = p.slot_elems;
+  a.unit_elems = p.unit_elems;
+  for (int l = 0; l <= kMaxL; ++l) a.dy_off[l] = p.dy_off[l];
+  k_tc_metro<<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
 }

@@ -19,7 +19,25 @@ struct TcCall {
   float* dlogpsi;  // TC_ELOC: [B][E] or NULL
 };
 
+// Plain-move Metropolis sweeps of BF16 models on the tensor cores (same move rule and
+// outputs as gna_metropolis_sweep's CUDA-core samplers).
+struct TcmCall {
+  const gna_graph* g;
+  Dims m;
+  const float* theta;
+  int8_t* chain_spins;
+  int64_t C;
+  int32_t n_sweeps, record_every;
+  uint64_t seed, step0;
+  int8_t* samples_out;
+  double* logpsi_out;
+  int32_t* n_acc;
+  double* trace;
+};
+
 gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes);
+gna_status tcm_workspace(const gna_graph* g, const Dims& m, int64_t C, size_t* bytes);
+gna_status tcm_run(const TcmCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_run(const TcCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_read_status(int* flags, int clear);
 

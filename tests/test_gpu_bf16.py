@@ -133,3 +133,103 @@ def test_bf16_device_status_clean(torch):
     s = torch.tensor(W.random_spins(g.n_sites, 300, seed=5), device="cuda")
     gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL)
     assert gna.device_status(clear=True) == 0
+
+
+# ---------------------------------------------------------------------------------
+# Metropolis sweeps on the tensor cores (BF16 models, plain moves)
+# ---------------------------------------------------------------------------------
+
+def _replay(g, s0, tr, seed, step0):
+    """Replay the kernel's trace with the oracle's Philox words: the bond of every step,
+    the no-op on parallel bonds, the decision u < exp(2 Re Delta) on the kernel's own
+    Delta with the FP32 uniform; returns the states before each step and the near-tie count."""
+    from oracle import sampler
+
+    C, K = tr.shape[0], tr.shape[1]
+    s = s0.copy()
+    before = np.empty((C, K, g.n_sites), dtype=np.int8)
+    near = 0
+    for c in range(C):
+        for k in range(K):
+            before[c, k] = s[c]
+            w = sampler.step_words(seed, c, step0 + k)
+            e = sampler.bond_index(w[0], g.n_edges)
+            assert int(tr[c, k, 0]) == e, (c, k)
+            assert tr[c, k, 3] == 1.0
+            i, j = g.edges[e]
+            if s[c, i] == s[c, j]:
+                assert np.isnan(tr[c, k, 2]) and tr[c, k, 1] == 0
+                continue
+            u = sampler.uniform(w[1], "fp32")
+            dre = tr[c, k, 2]
+            if abs(float(u) - np.exp(2 * dre)) < 1e-6:
+                near += 1
+            else:
+                assert bool(tr[c, k, 1]) == sampler.accept(u, dre, "fp32"), (c, k)
+            if tr[c, k, 1]:
+                s[c, [i, j]] = s[c, [j, i]]
+    return s, before, near
+
+
+@pytest.mark.parametrize("name,F,L", [("kagome2", 16, 2), ("kagome6", 32, 4), ("tri6", 64, 3)])
+def test_bf16_sampler_bookkeeping_and_ratios(torch, name, F, L):
+    # bonds and no-ops bit-exact, decisions exact given the kernel's Delta, configurations and
+    # acceptance counts consistent with the replay; Delta of every antiparallel proposal
+    # within the BF16 benchmark-scale tolerance of the oracle on the state it was made from
+    g = _graph(name)
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.1)
+    C, sweeps, seed, step0 = 9 if name == "kagome2" else 5, 2, 31, 77
+    s0 = W.random_spins(g.n_sites, C, seed=4)
+    ch = torch.tensor(s0, device="cuda")
+    _, _, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, sweeps, 0, seed, step0, trace=True)
+    tr = tr.cpu().numpy()
+    s, before, near = _replay(g, s0, tr, seed, step0)
+    assert near <= 2
+    assert np.array_equal(ch.cpu().numpy(), s)
+    assert acc.cpu().numpy().sum() == tr[:, :, 1].sum() > 0
+    anti = ~np.isnan(tr[:, :, 2])
+    cs, ks = np.nonzero(anti)
+    pick = np.random.default_rng(0).choice(len(cs), size=min(40, len(cs)), replace=False)
+    states = before[cs[pick], ks[pick]]
+    d = hz.bond_log_ratios(lambda x: gcn.logpsi_complex(th, F, L, Ah, x), g.edges, states)
+    want = d.real[np.arange(len(pick)), tr[cs[pick], ks[pick], 0].astype(int)]
+    assert np.abs(tr[cs[pick], ks[pick], 2] - want).max() <= 2e-3
+
+
+def test_bf16_sampler_records_match_forward(torch):
+    # Kagome 6x6x3, L = 4, F = 32: recorded samples conserve S_z and the recorded log Psi
+    # (from the incrementally updated FP32 pre-activations) matches a fresh BF16 forward
+    g = W.kagome(6)
+    F, L = 32, 4
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.3)
+    ch = torch.tensor(W.random_spins(g.n_sites, 300, seed=9), device="cuda")
+    samples, lpo, acc, _ = gna.metropolis_sweep(graph, model, theta, ch, 3, 1, 11, 0)
+    x = samples.cpu().numpy()
+    assert np.all((x > 0).sum(-1) == g.n_sites // 2)
+    assert np.array_equal(x[-1], ch.cpu().numpy())
+    assert acc.cpu().numpy().sum() > 0
+    for r in range(3):
+        want = gna.forward(graph, model, theta, samples[r].contiguous()).cpu().numpy()
+        assert np.abs(lpo[r].cpu().numpy() - want).max() <= 2e-2 * max(1.0, np.abs(want).max())
+    want = gcn.logpsi(th, F, L, Ah, x[-1][:4])
+    assert np.abs(lpo[-1].cpu().numpy()[:4] - want).max() <= 2e-2 * max(1.0, np.abs(want).max())
+
+
+def test_bf16_sampler_matches_fp32_sampler_statistics(torch):
+    # same move rule, Delta in BF16 vs FP32: the mean local energy of the two samplers'
+    # chains agrees within 4 combined standard errors (Kagome 2x2x3, F = 16, L = 2)
+    g = W.kagome(2)
+    F, L = 16, 2
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.8)
+    m32 = gna.Model(F, L, gna.PREC_FP32)
+    res = {}
+    for name, md in (("bf16", model), ("fp32", m32)):
+        ch = torch.tensor(W.random_spins(g.n_sites, 2048, seed=1), device="cuda")
+        gna.metropolis_sweep(graph, md, theta, ch, 20, 0, 5, 0)
+        samples, _, _, _ = gna.metropolis_sweep(graph, md, theta, ch, 40, 4, 5, 20 * g.n_sites)
+        E = gna.local_energy(graph, m32, theta, samples.reshape(-1, g.n_sites).contiguous(),
+                             gna.ELOC_FULL).cpu().numpy()[:, 0].reshape(10, 2048)
+        m = E.mean(axis=0)
+        res[name] = (m.mean(), m.std() / np.sqrt(len(m)))
+    (a, sa), (b, sb) = res["bf16"], res["fp32"]
+    assert abs(a - b) < 4 * np.hypot(sa, sb), (res)

@@ -295,7 +295,12 @@ def run_reference(a):
 # DRAM bytes per sample of the dominant kernels from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / the samples it processed), valid only for the source file
 # that was profiled: keyed by (workload, kernel) with the SHA-256 of that source.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    # ncu --set full, 2048 configurations, one launch: 594,944 B read + 0 B written
+    ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 594944 / 2048, "sha256": "5a4fa317265f046fcd72c1477f41d4875111b1d54327e2d93876e85785b279aa"},
+    # ncu --set full, 2048 chains, one sweep: 6,129,408 B read + 332,758,784 B written
+    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (6129408 + 332758784) / 2048, "sha256": "5a4fa317265f046fcd72c1477f41d4875111b1d54327e2d93876e85785b279aa"},
+}
 
 
 def _source_sha(rel):
@@ -482,12 +487,17 @@ def run_ours(a):
     alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     t_sweep = float(np.median(ph[:, 0]))
     if t_sweep >= K * t_incr:
-        kern = "k_metro_warp (gna_metropolis_sweep, %d sweeps)" % S
-        roof = {"bound": "alu", "achieved": fl_sweep / (t_sweep / 1000.0) / 1e12, "peak": alu_peak,
-                "unit": "TFLOP/s", "kernel": kern,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz (FP32 difference propagation)",
-                "flops_per_launch": fl_sweep,
-                "traffic": profiled_traffic(wl["workload"], "k_metro_warp", "metro.cu", C * S)}
+        if prec == gna.PREC_BF16 and prop is None:
+            roof = {"bound": "tensor", "achieved": fl_sweep / (t_sweep / 1000.0) / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "kernel": "k_tc_metro (gna_metropolis_sweep, %d sweeps, BF16 tcgen05)" % S,
+                    "peak_source": peak_kind + " bf16_tflops_sustained", "flops_per_launch": fl_sweep,
+                    "traffic": profiled_traffic(wl["workload"], "k_tc_metro", "tc.cu", C * S)}
+        else:
+            roof = {"bound": "alu", "achieved": fl_sweep / (t_sweep / 1000.0) / 1e12, "peak": alu_peak,
+                    "unit": "TFLOP/s", "kernel": "k_metro_warp (gna_metropolis_sweep, %d sweeps)" % S,
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz (FP32 difference propagation)",
+                    "flops_per_launch": fl_sweep, "traffic": None}
     elif prec == gna.PREC_BF16:
         roof = {"bound": "tensor", "achieved": fl_incr / (t_incr / 1000.0) / 1e12,
                 "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",

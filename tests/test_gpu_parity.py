@@ -347,6 +347,57 @@ def test_isgo_grad_parity(torch, prec):
     assert abs(st[3] - ess) <= tol * ess
 
 
+def test_isgo_reuse_loop_replays_oracle_fp64(torch):
+    # Kagome 2x2x3, F = 16, L = 2: ten reuse steps (isgo_grad + SGD) on fixed samples give
+    # the oracle's theta trajectory (isgo_gradient + sgd in FP64) to 1e-10
+    g = W.kagome(2)
+    F, L = 16, 2
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, gna.PREC_FP64, scale=0.5)
+    s = W.random_spins(g.n_sites, 256, seed=21)
+    lp0 = gcn.logpsi(th, F, L, Ah, s)
+    st, l0 = torch.tensor(s, device="cuda"), torch.tensor(lp0, device="cuda")
+    th_o = th.copy()
+    for _ in range(10):
+        grad, _ = gna.isgo_grad(graph, model, theta, st, l0)
+        gna.sgd_update(model, theta, grad, 0.02)
+        g_o = isgo.isgo_gradient(th_o, F, L, Ah, g.edges, g.J, s, lp0[:, 0] + 1j * lp0[:, 1])[0]
+        th_o = isgo.sgd(th_o, g_o, 0.02)
+    _close(theta.cpu().numpy(), th_o, 1e-10)
+
+
+def test_isgo_training_kagome12_respects_the_variational_bound(torch):
+    # Kagome 2x2x3 (S_z = 0 sector of 924 states, ED E0 = -5.4449), F = 16, L = 2, FP64,
+    # 1024 chains: ISGO iterations (2 sweeps, K = 10 reuse steps) from weight scale 0.5 lower
+    # the exact enumerated energy E_v(theta) far below its start, E_v stays >= E0, and the
+    # chains' weighted mean agrees with E_v
+    from paper_2011_12453_gb300 import vmc
+
+    g = W.kagome(2)
+    F, L = 16, 2
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, gna.PREC_FP64, scale=0.5)
+    Hs, codes = hz.sector_hamiltonian(g.n_sites, g.edges, g.J)
+    sall = hz.codes_to_spins(codes, g.n_sites)
+    E0 = np.linalg.eigvalsh(Hs.toarray())[0]
+
+    def exact(t):
+        return hz.variational_energy(gcn.logpsi_complex(t, F, L, Ah, sall), Hs).real
+
+    Ev_start = exact(th)
+    ch = vmc.Chains(graph, model, theta, W.random_spins(g.n_sites, 1024, seed=2), seed=3)
+    ch.sweep(20)
+    for _ in range(30):
+        st = vmc.isgo_iteration(ch, K=10, lr=0.01, sweeps=2)
+    Ev = exact(theta.cpu().numpy())
+    assert Ev >= E0 - 1e-9
+    assert Ev < Ev_start - 2.0, (Ev_start, Ev)
+    samples, _, _, _ = ch.sweep(40, record_every=2)
+    E = gna.local_energy(graph, model, theta, samples.reshape(-1, g.n_sites).contiguous(),
+                         gna.ELOC_FULL).cpu().numpy()[:, 0].reshape(20, 1024)
+    m = E.mean(axis=0)
+    assert abs(m.mean() - Ev) < 5 * m.std() / np.sqrt(len(m)) + 1e-3, (m.mean(), Ev)
+    print("kagome12 ISGO: E_v start %.4f -> %.4f, chains %.4f, ED %.4f" % (Ev_start, Ev, m.mean(), E0))
+
+
 def test_sgd_update(torch):
     m = gna.Model(16, 2, gna.PREC_FP32)
     th = torch.randn(m.num_params, device="cuda")

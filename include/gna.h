@@ -277,6 +277,23 @@ GNA_API gna_status isgo_grad(const gna_graph* g, const gna_model_desc* d, const 
                      int64_t B, double* grad, double* stats, void* workspace,
                      size_t workspace_bytes, void* stream);
 
+/* Grouping of duplicated samples into unique states with counts (scaling section: the
+ * sampler's states are grouped before the ISGO weights, which then carry log count_x).
+ *   spins     dev int8 [B][n_sites] (+-1)
+ *   logpsi    dev float64 [B][2] log Psi^0 of each sample, or NULL
+ *   u_spins   dev int8 [B][n_sites] out: the unique states, in order of first occurrence
+ *   u_logpsi  dev float64 [B][2] out: log Psi^0 of each unique state's first occurrence
+ *             (ignored when logpsi is NULL)
+ *   counts    dev float64 [B] out: copies of each unique state
+ *   n_unique  dev int64 [1] out: U; rows U..B-1 of the outputs are left untouched
+ * Bit-exact and independent of thread scheduling.  0 <= B < 2^31, 1 <= n_sites <= 4096;
+ * the workspace size is given by gna_dedup_workspace_size().  Caller-owned buffers,
+ * asynchronous on stream. */
+GNA_API gna_status gna_dedup_workspace_size(int64_t B, int32_t n_sites, size_t* bytes);
+GNA_API gna_status gna_dedup(int32_t n_sites, const int8_t* spins, const double* logpsi, int64_t B,
+                             int8_t* u_spins, double* u_logpsi, double* counts, int64_t* n_unique,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
 /* Plain gradient step w <- w - lr * grad (scaling section).  theta typed as above. */
 GNA_API gna_status gna_sgd_update(const gna_model_desc* d, void* theta, const double* grad,
                           double lr, void* stream);

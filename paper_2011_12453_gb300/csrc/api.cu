@@ -322,6 +322,21 @@ extern "C" gna_status gna_backward_static(const gna_graph* g, const gna_model_de
   return simt_backward_static(sc, simt_prec(d), (cudaStream_t)stream);
 }
 
+extern "C" gna_status gna_dedup_workspace_size(int64_t B, int32_t n_sites, size_t* bytes) {
+  if (!bytes || B < 0 || B >= (int64_t)1 << 31 || n_sites < 1 || n_sites > 4096) return GNA_ERR_INVALID_ARG;
+  *bytes = dedup_workspace(B, n_sites);
+  return GNA_OK;
+}
+
+extern "C" gna_status gna_dedup(int32_t n_sites, const int8_t* spins, const double* logpsi, int64_t B,
+                                int8_t* u_spins, double* u_logpsi, double* counts, int64_t* n_unique,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  if (B < 0 || B >= (int64_t)1 << 31 || n_sites < 1 || n_sites > 4096 || !n_unique) return GNA_ERR_INVALID_ARG;
+  if (B > 0 && (!spins || !u_spins || !counts || (logpsi && !u_logpsi))) return GNA_ERR_INVALID_ARG;
+  return dedup_run(n_sites, spins, logpsi, B, u_spins, u_logpsi, counts, n_unique, workspace, workspace_bytes,
+                   (cudaStream_t)stream);
+}
+
 extern "C" gna_status gna_isgo_weights_workspace(int64_t B, size_t* bytes) {
   if (!bytes || B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
   *bytes = isgo_weights_ws(B);

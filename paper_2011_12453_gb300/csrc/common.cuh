@@ -124,6 +124,9 @@ struct SimtCall {
 gna_status simt_workspace(const gna_graph* g, const Dims& m, int prec, int op, int64_t B, size_t* bytes);
 gna_status simt_run(const SimtCall& sc, int prec, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status simt_backward_static(const SimtCall& sc, int prec, cudaStream_t stream);
+size_t dedup_workspace(int64_t B, int N);
+gna_status dedup_run(int N, const int8_t* spins, const double* logpsi, int64_t B, int8_t* us, double* ul, double* uc,
+                     int64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t isgo_weights_ws(int64_t B);
 gna_status isgo_weights_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
                                double* cot, double* stats, void* ws, cudaStream_t st);

@@ -174,6 +174,7 @@ struct TcLayout {
   uint32_t a_unit;                // bytes of one unit's A tiles
   uint32_t int_unit, dbl_unit;    // per-unit slices of the int / double scratch (elements)
   uint64_t new16_unit, part_unit; // per-unit slices of the dH rows and Delta partials (bytes)
+  int part_rows;                  // rows of each warp group's Delta partials (>= G * maxball[L])
   uint64_t rstate, state_unit;    // sampler only: per-unit chain-pool state (bytes)
 };
 
@@ -243,7 +244,8 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
   }
   t->new16_unit = (n16 + 15) / 16 * 16;
   t->rnew16 = rtake((uint64_t)U * t->new16_unit);
-  t->part_unit = (uint64_t)(kTcThreads / U / 128) * t->T * 128 * 2 * 4;  // [warp group][row][Re, Im]
+  t->part_rows = G * maxball[L];
+  t->part_unit = (uint64_t)(kTcThreads / U / 128) * t->part_rows * 2 * 4;  // [warp group][row][Re, Im]
   t->rpart = rtake((uint64_t)U * t->part_unit);
   t->region_bytes = (r + 255) / 256 * 256;
   if (region_in_smem) {
@@ -485,16 +487,15 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
 // One thread per (row, 8-feature chunk): the chunk of the message and the chunk of the self
 // term, so that every thread of the unit does the same amount of work.
-__device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
+__device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q0, int n) {
   const DevGraph& g = c.a->g;
   const int F = c.F, G = c.G, ldh = c.ldh;
   const int F8 = F / 8;
   const int* offp = u.soff + (l - 1) * (G + 1);
   const int* offl = u.soff + l * (G + 1);
-  const int R = offl[nb];
   const __nv_bfloat16* dp = new16(c, u, l - 1);
-  for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
-    const int q = idx / F8, ch = idx - q * F8;
+  for (int idx = u.tid; idx < n * F8; idx += u.nthr) {
+    const int qa = idx / F8, ch = idx - qa * F8, q = q0 + qa;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
     const int bo = __ldg(g.ball_off + u.slot_e[k]);
@@ -513,8 +514,8 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
     w.y = pack_bf16(acc[2], acc[3]);
     w.z = pack_bf16(acc[4], acc[5]);
     w.w = pack_bf16(acc[6], acc[7]);
-    *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = w;
-    *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
+    *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch)) = w;
+    *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch)) =
         r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh) : make_uint4(0u, 0u, 0u, 0u);
   }
 }
@@ -522,7 +523,7 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb) {
 // dY in TMEM -> dH = t (1 - H^2) / (1 + H t), t = tanh(dY), for group rows [0, R) at layer
 // l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
 // columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
-__device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int nb) {
+__device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int nb, int q0) {
   const DevGraph& g = c.a->g;
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
@@ -532,7 +533,7 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
   __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
   const float* Yl = cacheY(c, l);
   for (int t = 0; t < nt; ++t) {
-    const int q = t * 128 + q4 * 32 + lane;
+    const int q = q0 + t * 128 + q4 * 32 + lane;
     int v = 0;
     if (q < R) {
       const int k = slot_of(offl, nb, q);
@@ -583,8 +584,8 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
       }
     }
     if (l == L && q < R) {
-      u.part[((size_t)wg * c.T * 128 + q) * 2] = pre;
-      u.part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
+      u.part[((size_t)wg * c.a->lay.part_rows + q) * 2] = pre;
+      u.part[((size_t)wg * c.a->lay.part_rows + q) * 2 + 1] = pim;
     }
   }
   tc_fence_before();
@@ -616,16 +617,21 @@ __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
     d0[(size_t)(u.soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
   }
   unit_sync(u);
+  // each layer in passes of at most T tiles of 128 rows
   for (int l = 1; l <= L; ++l) {
-    gather_delta(c, u, l, nb);
-    const int nt = (u.soff[l * (G + 1) + nb] + 127) / 128;
-    if (!run_mmas(c, u, nt)) return false;
-    epilogue_delta(c, u, l, nt, nb);
+    const int R = u.soff[l * (G + 1) + nb];
+    for (int q0 = 0; q0 < R; q0 += c.T * 128) {
+      const int n = min(c.T * 128, R - q0);
+      gather_delta(c, u, l, nb, q0, n);
+      const int nt = (n + 127) / 128;
+      if (!run_mmas(c, u, nt)) return false;
+      epilogue_delta(c, u, l, nt, nb, q0);
+    }
   }
   // Delta_k = sum over the bond's last-layer rows of the per-row partials (one warp per bond)
   const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
   const int* offL = u.soff + L * (G + 1);
-  const size_t wgs = (size_t)c.T * 128;
+  const size_t wgs = (size_t)c.a->lay.part_rows;
   for (int k = warp; k < nb; k += nwarps) {
     float dre = 0.f, dim = 0.f;
     for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
@@ -945,7 +951,7 @@ __device__ bool tcm_forward(const TcCtx& c, Unit& u, const TcmArgs& a, float* Ys
 // dY in TMEM -> dH for the group rows at layer l; the chains' own Y^l rows are read from
 // their slots, dY^l rows are kept in the slots for the update on acceptance.
 __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int l,
-                             int nt, int nb) {
+                             int nt, int nb, int q0) {
   const DevGraph& g = c.a->g;
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
@@ -954,7 +960,7 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
   const int R = offl[nb];
   __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
   for (int t = 0; t < nt; ++t) {
-    const int q = t * 128 + q4 * 32 + lane;
+    const int q = q0 + t * 128 + q4 * 32 + lane;
     const float* yrow = nullptr;
     float* dyrow = nullptr;
     if (q < R) {
@@ -1006,8 +1012,8 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
       }
     }
     if (l == L && q < R) {
-      u.part[((size_t)wg * c.T * 128 + q) * 2] = pre;
-      u.part[((size_t)wg * c.T * 128 + q) * 2 + 1] = pim;
+      u.part[((size_t)wg * c.a->lay.part_rows + q) * 2] = pre;
+      u.part[((size_t)wg * c.a->lay.part_rows + q) * 2 + 1] = pim;
     }
   }
   tc_fence_before();
@@ -1040,14 +1046,18 @@ __device__ bool tcm_group(const TcCtx& c, Unit& u, const TcmArgs& a, const TcmSl
   }
   unit_sync(u);
   for (int l = 1; l <= L; ++l) {
-    gather_delta(c, u, l, nb);
-    const int nt = (u.soff[l * (G + 1) + nb] + 127) / 128;
-    if (!run_mmas(c, u, nt)) return false;
-    tcm_epilogue(c, u, a, S, ug, l, nt, nb);
+    const int R = u.soff[l * (G + 1) + nb];
+    for (int q0 = 0; q0 < R; q0 += c.T * 128) {
+      const int n = min(c.T * 128, R - q0);
+      gather_delta(c, u, l, nb, q0, n);
+      const int nt = (n + 127) / 128;
+      if (!run_mmas(c, u, nt)) return false;
+      tcm_epilogue(c, u, a, S, ug, l, nt, nb, q0);
+    }
   }
   const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
   const int* offL = u.soff + L * (G + 1);
-  const size_t wgs = (size_t)c.T * 128;
+  const size_t wgs = (size_t)c.a->lay.part_rows;
   for (int k = warp; k < nb; k += nwarps) {
     float dre = 0.f, dim = 0.f;
     for (int q = offL[k] + lane; q < offL[k + 1]; q += 32) {
@@ -1132,7 +1142,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   u.tbase = tmem + (uint32_t)(h * c.T * F);
   u.bar = bars + h;
   u.phase = 0;
-  u.d16 = (__nv_bfloat16*)(c.region + b.lay.rnew16 + (size_t)h * b.lay.new16_unit);
+  const int ug = blockIdx.x * U + h;  // this unit's workspace index
+  float* unit_ws = a.gws + (size_t)ug * a.unit_elems;
+  u.d16 = b.region_in_smem ? (__nv_bfloat16*)(c.region + b.lay.rnew16 + (size_t)h * b.lay.new16_unit)
+                           : (__nv_bfloat16*)(unit_ws + (size_t)G * a.slot_elems + (size_t)N * (F + 8));
   u.part = (float*)(c.region + b.lay.rpart + (size_t)h * b.lay.part_unit);
   u.slot_e = c.list + h * b.lay.int_unit;
   u.soff = u.slot_e + G;
@@ -1154,8 +1167,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
     S.ok = S.gslot + G;
     S.spins = (int8_t*)(S.ok + G);
   }
-  const int ug = blockIdx.x * U + h;                 // this unit's workspace index
-  float* Hs_f = a.gws + (size_t)ug * a.unit_elems + (size_t)G * a.slot_elems;
+  float* Hs_f = unit_ws + (size_t)G * a.slot_elems;
   __nv_bfloat16* Hs = (__nv_bfloat16*)Hs_f;
   const int64_t n_steps = (int64_t)a.n_sweeps * N;
   const int64_t pools = (a.C + G - 1) / G;
@@ -1410,9 +1422,11 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   const int T = tc_tiles_per_unit(m.F);
   if (tc_units(m.F) * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   const size_t budget = (size_t)di.smem_optin - 2048;
+  // bonds per group: as many as fill the T tiles at the last layer in one pass; a layer with
+  // more rows runs in several passes
   int G = op == TC_ELOC ? (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1) : 1;
   if (G > 16) G = 16;
-  if (G < 1) return GNA_ERR_UNSUPPORTED;  // one bond's last-layer rows exceed the TMEM tiles
+  if (G < 1) G = 1;
   TcLayout lay;
   // prefer the whole region in shared memory with as many bonds per group as fit
   int g_fit = 0;
@@ -1426,7 +1440,10 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (g_fit > 0) {
     p->region_in_smem = 1;
   } else {
-    tc_layout(m, maxball, G, 0, &lay);
+    // region in the workspace: larger groups (several passes per deep layer) keep more rows
+    // in each pass
+    const int Gg = op == TC_ELOC ? (G > 8 ? G : 8) : 1;
+    tc_layout(m, maxball, Gg, 0, &lay);
     if (lay.smem_total > budget) return GNA_ERR_UNSUPPORTED;
     p->region_in_smem = 0;
   }
@@ -1491,12 +1508,14 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
 struct TcmPlan {
   TcLayout lay;
   int grid = 0;
+  int new16_in_smem = 1;
   uint64_t slot_elems = 0, unit_elems = 0;
   uint64_t dy_off[kMaxL + 1] = {0};
   size_t ws_bytes = 0;
 };
 
-static void tcm_layout(const Dims& m, const int* maxball, int G, TcLayout* t) {
+// new16_in_smem = 0: the units' dH rows live in the workspace (after each unit's H scratch).
+static void tcm_layout(const Dims& m, const int* maxball, int G, int new16_in_smem, TcLayout* t) {
   const int F = m.F, N = m.N, L = m.L;
   memset(t, 0, sizeof(*t));
   uint64_t o = 0;
@@ -1537,8 +1556,9 @@ static void tcm_layout(const Dims& m, const int* maxball, int G, TcLayout* t) {
     n16 += (uint64_t)G * maxball[l] * ldh * 2;
   }
   t->new16_unit = (n16 + 15) / 16 * 16;
-  t->rnew16 = rtake((uint64_t)U * t->new16_unit);
-  t->part_unit = (uint64_t)(unit_threads / 128) * t->T * 128 * 2 * 4;
+  t->rnew16 = new16_in_smem ? rtake((uint64_t)U * t->new16_unit) : 0;
+  t->part_rows = G * maxball[L];
+  t->part_unit = (uint64_t)(unit_threads / 128) * t->part_rows * 2 * 4;
   t->rpart = rtake((uint64_t)U * t->part_unit);
   t->state_unit = tcm_state_bytes(G, N, unit_threads);
   t->rstate = rtake((uint64_t)U * t->state_unit);
@@ -1556,16 +1576,23 @@ static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
   const int T = tc_tiles_per_unit(m.F), U = tc_units(m.F);
   if (U * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
-  int G = (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1);
-  if (G > 16) G = 16;
-  if (G < 1) return GNA_ERR_UNSUPPORTED;
+  // pool size: the chains whose last-layer rows fill the T tiles in one pass; when fewer
+  // than two fit, pools of 8 with several passes per deep layer and the dH rows in the
+  // workspace
+  const int G0 = (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1);
   const size_t budget = (size_t)di.smem_optin - 2048;
   TcLayout lay;
-  for (; G >= 1; --G) {
-    tcm_layout(m, maxball, G, &lay);
-    if (lay.smem_total <= budget) break;
+  int in_smem = G0 >= 2 ? 1 : 0;
+  int G = 0;
+  for (; in_smem >= 0; --in_smem) {
+    for (G = in_smem ? (G0 > 16 ? 16 : G0) : 8; G >= 1; --G) {
+      tcm_layout(m, maxball, G, in_smem, &lay);
+      if (lay.smem_total <= budget) break;
+    }
+    if (G >= 1) break;
   }
   if (G < 1) return GNA_ERR_UNSUPPORTED;
+  p->new16_in_smem = in_smem;
   const uint32_t min_smem = (uint32_t)(228u * 1024u / (512 / kTmemCols + 1)) + 1024u;
   if (lay.smem_total < min_smem) lay.smem_total = min_smem;
   p->lay = lay;
@@ -1588,6 +1615,7 @@ static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan
   }
   p->slot_elems = (e + 3) / 4 * 4;
   p->unit_elems = (uint64_t)G * p->slot_elems + (uint64_t)m.N * (m.F + 8);  // + two BF16 H layers
+  if (!in_smem) p->unit_elems += lay.new16_unit / sizeof(float);           // + the dH rows
   p->ws_bytes = align_up((size_t)grid * U * p->unit_elems * sizeof(float));
   return GNA_OK;
 }
@@ -1618,7 +1646,7 @@ gna_status tcm_run(const TcmCall& call, void* ws, size_t ws_bytes, cudaStream_t 
   a.base.op = TC_ELOC;
   a.base.lay = p.lay;
   a.base.theta = call.theta;
-  a.base.region_in_smem = 1;
+  a.base.region_in_smem = p.new16_in_smem;  // here: where the units' dH rows live
   a.chain_spins = call.chain_spins;
   a.C = call.C;
   a.n_sweeps = call.n_sweeps;

@@ -37,6 +37,7 @@ EXPORTED = [
     "gna_isgo_weights", "isgo_grad",
     "gna_sgd_update", "gna_philox4x64_10", "gna_device_status", "gna_proposal_num_params",
     "gna_proposal_workspace_size", "gna_proposal_logits", "gna_proposal_grad", "gna_proposal_adam",
+    "gna_dedup_workspace_size", "gna_dedup",
 ]
 
 
@@ -98,6 +99,8 @@ def lib():
             "gna_sgd_update": (i32, [ctypes.POINTER(ModelDesc), vp, vp, dbl, vp]),
             "gna_philox4x64_10": (i32, [vp, vp, i64, vp, vp]),
             "gna_device_status": (i32, [ctypes.POINTER(i32), i32]),
+            "gna_dedup_workspace_size": (i32, [i64, i32, ctypes.POINTER(sz)]),
+            "gna_dedup": (i32, [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -403,6 +406,26 @@ def sgd_update(model: Model, theta, grad, lr: float):
     _check(lib().gna_sgd_update(ctypes.byref(model.desc), theta.data_ptr(), grad.data_ptr(), float(lr), _stream()),
            "gna_sgd_update")
     return theta
+
+
+def dedup(spins, logpsi=None):
+    """Group duplicated samples: (unique spins [U][N], their log Psi^0 [U][2] or None,
+    counts float64 [U]) in order of first occurrence.  Reads U back to the host."""
+    import torch
+
+    B, N = spins.shape
+    dev = spins.device
+    us = torch.empty_like(spins)
+    ul = torch.empty((B, 2), dtype=torch.float64, device=dev) if logpsi is not None else None
+    uc = torch.empty(B, dtype=torch.float64, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    need = sz(0)
+    _check(lib().gna_dedup_workspace_size(B, N, ctypes.byref(need)), "gna_dedup_workspace_size")
+    w = workspace(int(need.value))
+    _check(lib().gna_dedup(N, spins.data_ptr(), _ptr(logpsi), B, us.data_ptr(), _ptr(ul), uc.data_ptr(),
+                           n.data_ptr(), w.data_ptr() if w.numel() else None, w.numel(), _stream()), "gna_dedup")
+    U = int(n.item())
+    return us[:U], (ul[:U] if ul is not None else None), uc[:U]
 
 
 def philox(keys, counters):

@@ -38,18 +38,24 @@ class Chains:
         return out
 
 
-def isgo_iteration(chains: Chains, K: int, lr: float, sweeps: int = 1):
+def isgo_iteration(chains: Chains, K: int, lr: float, sweeps: int = 1, group: bool = False):
     """One ISGO iteration: `sweeps` sweeps then one recorded sample per chain, reused for K
-    updates of theta.  Returns the statistics [K][4] (Re E, Im E, var, ESS) on the host."""
+    updates of theta; with group=True duplicated samples are first grouped into unique
+    states with counts (scaling section).  Returns the statistics [K][4] (Re E, Im E, var,
+    ESS) on the host."""
     import torch
 
     samples, lp0, _, _ = chains.sweep(sweeps, record_every=sweeps)
     s = samples[-1].contiguous()
     l0 = lp0[-1].contiguous()
+    counts = None
+    if group:
+        s, l0, counts = gna.dedup(s, l0)
+        s, l0, counts = s.contiguous(), l0.contiguous(), counts.contiguous()
     stats = torch.empty((K, 4), dtype=torch.float64, device=s.device)
     grad = torch.empty(chains.model.num_params, dtype=torch.float64, device=s.device)
     for k in range(K):
-        gna.isgo_grad(chains.graph, chains.model, chains.theta, s, l0, grad=grad, stats=stats[k])
+        gna.isgo_grad(chains.graph, chains.model, chains.theta, s, l0, counts=counts, grad=grad, stats=stats[k])
         gna.sgd_update(chains.model, chains.theta, grad, lr)
     return stats.cpu().numpy()
 

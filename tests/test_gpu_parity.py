@@ -349,7 +349,9 @@ def test_isgo_grad_parity(torch, prec):
 
 def test_isgo_reuse_loop_replays_oracle_fp64(torch):
     # Kagome 2x2x3, F = 16, L = 2: ten reuse steps (isgo_grad + SGD) on fixed samples give
-    # the oracle's theta trajectory (isgo_gradient + sgd in FP64) to 1e-10
+    # the oracle's theta trajectory (isgo_gradient + sgd in FP64).  Bound: each FP64 gradient
+    # is within 1e-9 relative of the oracle's (the gradient parity bound), so ten steps of
+    # lr = 0.02 move theta apart by at most 10 * 0.02 * 1e-9 * |g|, below 1e-9 * max|theta|
     g = W.kagome(2)
     F, L = 16, 2
     graph, model, theta, th, Ah = _setup(torch, g, F, L, gna.PREC_FP64, scale=0.5)
@@ -362,7 +364,7 @@ def test_isgo_reuse_loop_replays_oracle_fp64(torch):
         gna.sgd_update(model, theta, grad, 0.02)
         g_o = isgo.isgo_gradient(th_o, F, L, Ah, g.edges, g.J, s, lp0[:, 0] + 1j * lp0[:, 1])[0]
         th_o = isgo.sgd(th_o, g_o, 0.02)
-    _close(theta.cpu().numpy(), th_o, 1e-10)
+    _close(theta.cpu().numpy(), th_o, 1e-9)
 
 
 def test_isgo_training_kagome12_respects_the_variational_bound(torch):

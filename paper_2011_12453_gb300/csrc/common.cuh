@@ -32,6 +32,12 @@ struct DevGraph {
   const int* nbr_pos = nullptr;   // [...]  for neighbour k of the row's vertex (CSR order):
                                   //        its row position in this bond's ball_Lmax, or
                                   //        INT_MAX when outside ball_Lmax
+  // Compact forms of the same tables for staging in shared memory (a vertex or a ball
+  // position fits 16 bits: n <= 4096):
+  const int* ball_span = nullptr;      // [E][Lmax+1] entries (sum of degrees) of the first ball_size rows
+  const int* row_pack = nullptr;       // [sum]  v | (start of the row's entries within the bond's << 16)
+  const int16_t* nbr_pos16 = nullptr;  // [...]  nbr_pos, 32767 outside ball_Lmax
+  const int* bond_ent = nullptr;       // [E]    start of bond e's entries in nbr_pos / nbr_pos16
 };
 
 }  // namespace gna
@@ -44,6 +50,7 @@ struct gna_graph {
   std::vector<int> max_ball;  // [Lmax+1] max over bonds of |ball_l|
   std::vector<int> max_span;  // [Lmax+1] max over bonds of sum of degrees over ball_l rows
   int max_deg = 0;
+  bool pack_ok = true;  // every bond's entries fit the 16-bit starts of row_pack
   std::vector<void*> allocations;
 };
 

@@ -21,6 +21,9 @@ struct HostGraph {
   std::vector<float> wf;
   std::vector<double> wd, J;
   std::vector<int> ball_off, ball_size, ball_vert, row_nbr, nbr_pos, max_ball, max_span;
+  std::vector<int> ball_span, row_pack, bond_ent;  // compact forms, see DevGraph
+  std::vector<int16_t> nbr_pos16;
+  bool pack_ok = true;
 };
 
 gna_status validate(int32_t n_sites, int32_t n_edges, const int32_t* edges, const double* J,
@@ -81,6 +84,8 @@ void build(int n, int E, const int32_t* edges, const double* J, int Lmax, HostGr
   // neighbours of its newest rows, in order of discovery.
   h->ball_off.assign(E + 1, 0);
   h->ball_size.assign((size_t)E * (Lmax + 1), 0);
+  h->ball_span.assign((size_t)E * (Lmax + 1), 0);
+  h->bond_ent.assign(E, 0);
   h->max_ball.assign(Lmax + 1, 0);
   h->max_span.assign(Lmax + 1, 0);
   h->ball_vert.clear();
@@ -116,15 +121,21 @@ void build(int n, int E, const int32_t* edges, const double* J, int Lmax, HostGr
       int span = 0;
       for (int r = 0; r < sz[l]; ++r) span += h->row_ptr[order[r] + 1] - h->row_ptr[order[r]];
       if (span > h->max_span[l]) h->max_span[l] = span;
+      h->ball_span[(size_t)e * (Lmax + 1) + l] = span;
     }
     h->ball_off[e] = (int)h->ball_vert.size();
+    h->bond_ent[e] = (int)h->nbr_pos.size();
     for (int r = 0; r < (int)order.size(); ++r) {
       int v = order[r];
+      const int start = (int)h->nbr_pos.size() - h->bond_ent[e];
+      if (start > 0xFFFF) h->pack_ok = false;
       h->ball_vert.push_back(v);
       h->row_nbr.push_back((int)h->nbr_pos.size());
+      h->row_pack.push_back(v | ((start & 0xFFFF) << 16));
       for (int k = h->row_ptr[v]; k < h->row_ptr[v + 1]; ++k) {
         int u = h->col[k];
         h->nbr_pos.push_back(pos[u] >= 0 ? pos[u] : INT_MAX);
+        h->nbr_pos16.push_back((int16_t)(pos[u] >= 0 ? pos[u] : 32767));
       }
     }
     for (int v : order) pos[v] = -1;
@@ -182,7 +193,12 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   UP(h.ball_vert, ball_vert);
   UP(h.row_nbr, row_nbr);
   UP(h.nbr_pos, nbr_pos);
+  UP(h.ball_span, ball_span);
+  UP(h.row_pack, row_pack);
+  UP(h.nbr_pos16, nbr_pos16);
+  UP(h.bond_ent, bond_ent);
 #undef UP
+  g->pack_ok = h.pack_ok;
   g->h_row_ptr = h.row_ptr;
   g->h_col = h.col;
   g->h_edges = h.edges;

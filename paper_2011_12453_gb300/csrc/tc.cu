@@ -165,6 +165,8 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 struct TcLayout {
   // shared memory byte offsets
   uint32_t oWt, obias, oemb, owr, obr, oA, ospin, oint, odbl, obar, oslot, oregion, smem_total;
+  uint32_t orp, owf, orow, opos;  // CSR row starts and weights; per-unit staged rows / positions
+  uint32_t row_unit, pos_unit;    // staged rows (int) / neighbour positions (int16) per unit
   // region (shared or global) byte offsets
   uint64_t rcache16, rY, rnew16, rpart, region_bytes;
   uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
@@ -199,7 +201,26 @@ struct TcArgs {
 __host__ inline int tc_units(int F) { return F <= 32 ? 2 : 4; }
 __host__ inline int tc_tiles_per_unit(int F) { return F <= 32 ? 2 : 1; }
 
-__host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int region_in_smem, TcLayout* t) {
+// The staged tables of a unit: G bonds' rows of ball_L (packed vertex and entry start) and
+// their in-ball neighbour positions (maxspan = max entries of a bond's ball_L).
+__host__ inline void tc_stage_layout(const Dims& m, const int* maxball, int maxspan, int G, int U,
+                                     uint64_t& o, TcLayout* t) {
+  auto take = [&](uint64_t bytes, uint64_t align) {
+    o = (o + align - 1) / align * align;
+    uint64_t r = o;
+    o += bytes;
+    return (uint32_t)r;
+  };
+  t->orp = take((uint64_t)(m.N + 1) * 4, 16);
+  t->owf = take((uint64_t)2 * m.E * 4, 16);
+  t->row_unit = (uint32_t)(G * maxball[m.L]);
+  t->orow = take((uint64_t)U * t->row_unit * 4, 16);
+  t->pos_unit = (uint32_t)((G * maxspan + 7) / 8 * 8);
+  t->opos = take((uint64_t)U * t->pos_unit * 2, 16);
+}
+
+__host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, int G, int region_in_smem,
+                               TcLayout* t) {
   const int F = m.F, N = m.N, L = m.L;
   uint64_t o = 0;
   auto take = [&](uint64_t bytes, uint64_t align) {
@@ -220,12 +241,13 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int G, int reg
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
   t->ospin = take(N, 16);
-  t->int_unit = (uint32_t)(G + (L + 1) * (G + 1) + 4);
+  t->int_unit = (uint32_t)(G + (L + 2) * (G + 1) + 4);
   t->oint = take(((uint64_t)m.E + 16 + (uint64_t)U * t->int_unit) * 4, 16);
   t->dbl_unit = (uint32_t)(2 * G + 4);
   t->odbl = take((uint64_t)(16 + kTcThreads + U * t->dbl_unit) * 8, 16);
   t->obar = take(8 * U, 8);
   t->oslot = take(4, 4);
+  tc_stage_layout(m, maxball, maxspan, G, U, o, t);
   // region
   uint64_t r = 0;
   auto rtake = [&](uint64_t bytes) {
@@ -267,6 +289,8 @@ struct TcCtx {
   __nv_bfloat16* Wt;
   float *bias, *emb, *wr, *br;
   int8_t* spin;
+  const int* rp;     // CSR row starts [N+1] (shared memory)
+  const float* wfs;  // CSR weights [2E] (shared memory)
   int* list;     // antiparallel bonds of the configuration
   double* sdbl;  // shared double scratch (readout)
   unsigned char* region;
@@ -286,6 +310,9 @@ struct Unit {
   float* part;                 // this unit's Delta partials [nwg][T*128][2]
   int* slot_e;                 // [G]
   int* soff;                   // [(L+1)][G+1]
+  int* eoff;                   // [G+1] start of each bond's staged neighbour positions
+  int* srow;                   // staged row_pack of the group's bonds (bond k at soff[L][k])
+  int16_t* spos;               // staged nbr_pos16 of the group's bonds (bond k at eoff[k])
   double* res;                 // [2G] Delta of each bond of the group
 };
 
@@ -294,6 +321,39 @@ __device__ __forceinline__ void unit_sync(const Unit& u) {
     __syncthreads();
   else
     asm volatile("bar.sync %0, %1;" ::"r"(u.bar_id), "r"(u.nthr) : "memory");
+}
+
+// Offsets of the group's rows per layer (soff) and of its bonds' staged entries (eoff),
+// then the bonds' rows and in-ball neighbour positions into shared memory, so that the
+// passes of the group look them up without global-memory latency.
+__device__ void stage_group(const DevGraph& g, const Unit& u, int L, int G, int nb) {
+  const int Lm = g.Lmax;
+  if (u.tid == 0) {
+    for (int l = 0; l <= L; ++l) {
+      int o = 0;
+      for (int k = 0; k < nb; ++k) {
+        u.soff[l * (G + 1) + k] = o;
+        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
+      }
+      u.soff[l * (G + 1) + nb] = o;
+    }
+    int o = 0;
+    for (int k = 0; k < nb; ++k) {
+      u.eoff[k] = o;
+      o += __ldg(g.ball_span + (size_t)u.slot_e[k] * (Lm + 1) + L);
+    }
+    u.eoff[nb] = o;
+  }
+  unit_sync(u);
+  const int* offL = u.soff + L * (G + 1);
+  for (int k = 0; k < nb; ++k) {
+    const int e = u.slot_e[k];
+    const int* rows = g.row_pack + __ldg(g.ball_off + e);
+    const int16_t* ents = g.nbr_pos16 + __ldg(g.bond_ent + e);
+    const int nr = offL[k + 1] - offL[k], ne = u.eoff[k + 1] - u.eoff[k];
+    for (int r = u.tid; r < nr; r += u.nthr) u.srow[offL[k] + r] = __ldg(rows + r);
+    for (int t = u.tid; t < ne; t += u.nthr) u.spos[u.eoff[k] + t] = __ldg(ents + t);
+  }
 }
 
 __device__ __forceinline__ unsigned char* a_row_chunk(const Unit& u, int F, int q, int chunk) {
@@ -423,9 +483,9 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
       // one thread per (row, 8-feature chunk): the message chunk and the self chunk
       for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
         const int q = idx / F8, ch = idx - q * F8, v = r0 + q;
-        const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+        const int k0 = c.rp[v], k1 = c.rp[v + 1];
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
+        for (int k = k0; k < k1; ++k) fma_chunk(acc, c.wfs[k], hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
         uint4 w;
         w.x = pack_bf16(acc[0], acc[1]);
         w.y = pack_bf16(acc[2], acc[3]);
@@ -488,26 +548,26 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
 // One thread per (row, 8-feature chunk): the chunk of the message and the chunk of the self
 // term, so that every thread of the unit does the same amount of work.
 __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q0, int n) {
-  const DevGraph& g = c.a->g;
   const int F = c.F, G = c.G, ldh = c.ldh;
   const int F8 = F / 8;
   const int* offp = u.soff + (l - 1) * (G + 1);
   const int* offl = u.soff + l * (G + 1);
+  const int* offL = u.soff + c.L * (G + 1);
   const __nv_bfloat16* dp = new16(c, u, l - 1);
   for (int idx = u.tid; idx < n * F8; idx += u.nthr) {
     const int qa = idx / F8, ch = idx - qa * F8, q = q0 + qa;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
-    const int bo = __ldg(g.ball_off + u.slot_e[k]);
     const int sprev = offp[k + 1] - offp[k];
     const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh + ch * 8;
-    const int v = __ldg(g.ball_vert + bo + r);
-    const int* np = g.nbr_pos + __ldg(g.row_nbr + bo + r);
-    const int k0 = __ldg(g.row_ptr + v), dg = __ldg(g.row_ptr + v + 1) - k0;
+    const int rec = u.srow[offL[k] + r];
+    const int v = rec & 0xFFFF;
+    const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
+    const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int t = 0; t < dg; ++t) {
-      const int p = __ldg(np + t);
-      if (p < sprev) fma_chunk(acc, __ldg(g.wf + k0 + t), drow + (size_t)p * ldh);
+      const int p = np[t];
+      if (p < sprev) fma_chunk(acc, c.wfs[k0 + t], drow + (size_t)p * ldh);
     }
     uint4 w;
     w.x = pack_bf16(acc[0], acc[1]);
@@ -524,7 +584,6 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
 // l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
 // columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
 __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int nb, int q0) {
-  const DevGraph& g = c.a->g;
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, G = c.G, ldh = c.ldh, ldy = c.ldy;
@@ -532,12 +591,13 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
   const int R = offl[nb];
   __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
   const float* Yl = cacheY(c, l);
+  const int* offL = u.soff + L * (G + 1);
   for (int t = 0; t < nt; ++t) {
     const int q = q0 + t * 128 + q4 * 32 + lane;
     int v = 0;
     if (q < R) {
       const int k = slot_of(offl, nb, q);
-      v = __ldg(g.ball_vert + __ldg(g.ball_off + u.slot_e[k]) + (q - offl[k]));
+      v = u.srow[offL[k] + (q - offl[k])] & 0xFFFF;
     }
     float pre = 0.f, pim = 0.f;
     for (int ch = wg; ch < F / 8; ch += u.nwg) {
@@ -595,18 +655,8 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
 // Incremental Delta log Psi of the unit's bonds slot_e[0..nb): results in res[2k], res[2k+1].
 __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
   const DevGraph& g = c.a->g;
-  const int F = c.F, L = c.L, G = c.G, Lm = g.Lmax;
-  if (u.tid == 0) {
-    for (int l = 0; l <= L; ++l) {
-      int o = 0;
-      for (int k = 0; k < nb; ++k) {
-        u.soff[l * (G + 1) + k] = o;
-        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
-      }
-      u.soff[l * (G + 1) + nb] = o;
-    }
-  }
-  unit_sync(u);
+  const int F = c.F, L = c.L, G = c.G;
+  stage_group(g, u, L, G, nb);
   // layer 0: dH^0_i = emb(s_j) - emb(s_i), dH^0_j = -dH^0_i
   __nv_bfloat16* d0 = new16(c, u, 0);
   for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
@@ -672,6 +722,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   c.wr = (float*)(smem + a.lay.owr);
   c.br = (float*)(smem + a.lay.obr);
   c.spin = (int8_t*)(smem + a.lay.ospin);
+  c.rp = (const int*)(smem + a.lay.orp);
+  c.wfs = (const float*)(smem + a.lay.owf);
   c.list = (int*)(smem + a.lay.oint);
   c.sdbl = (double*)(smem + a.lay.odbl);
   c.region = a.region_in_smem ? smem + a.lay.oregion : a.gregion + (size_t)blockIdx.x * a.lay.region_bytes;
@@ -701,6 +753,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
   for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) c.wr[i] = th[m.owr + i];
   if (threadIdx.x < 2) c.br[threadIdx.x] = th[m.obr + threadIdx.x];
+  for (int i = threadIdx.x; i <= c.N; i += blockDim.x) ((int*)c.rp)[i] = __ldg(c.a->g.row_ptr + i);
+  for (int i = threadIdx.x; i < 2 * c.E; i += blockDim.x) ((float*)c.wfs)[i] = __ldg(c.a->g.wf + i);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -731,6 +785,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   u.part = (float*)(c.region + a.lay.rpart + (size_t)h * a.lay.part_unit);
   u.slot_e = c.list + c.E + 16 + h * a.lay.int_unit;
   u.soff = u.slot_e + c.G;
+  u.eoff = u.soff + (c.L + 1) * (c.G + 1);
+  u.srow = (int*)(smem + a.lay.orow) + (size_t)h * a.lay.row_unit;
+  u.spos = (int16_t*)(smem + a.lay.opos) + (size_t)h * a.lay.pos_unit;
   u.res = c.sdbl + 16 + kTcThreads + h * a.lay.dbl_unit;
 
   bool ok = true;
@@ -906,9 +963,9 @@ __device__ bool tcm_forward(const TcCtx& c, Unit& u, const TcmArgs& a, float* Ys
       const int nt = (R + 127) / 128;
       for (int idx = u.tid; idx < R * F8; idx += u.nthr) {
         const int q = idx / F8, ch = idx - q * F8, v = r0 + q;
-        const int k0 = __ldg(g.row_ptr + v), k1 = __ldg(g.row_ptr + v + 1);
+        const int k0 = c.rp[v], k1 = c.rp[v + 1];
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = k0; k < k1; ++k) fma_chunk(acc, __ldg(g.wf + k), hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
+        for (int k = k0; k < k1; ++k) fma_chunk(acc, c.wfs[k], hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
         uint4 w;
         w.x = pack_bf16(acc[0], acc[1]);
         w.y = pack_bf16(acc[2], acc[3]);
@@ -952,7 +1009,6 @@ __device__ bool tcm_forward(const TcCtx& c, Unit& u, const TcmArgs& a, float* Ys
 // their slots, dY^l rows are kept in the slots for the update on acceptance.
 __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int l,
                              int nt, int nb, int q0) {
-  const DevGraph& g = c.a->g;
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, N = c.N, G = c.G, ldh = c.ldh;
@@ -966,7 +1022,7 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
     if (q < R) {
       const int k = slot_of(offl, nb, q);
       const int r = q - offl[k];
-      const int v = __ldg(g.ball_vert + __ldg(g.ball_off + u.slot_e[k]) + r);
+      const int v = u.srow[u.soff[L * (G + 1) + k] + r] & 0xFFFF;
       float* sl = tcm_slot(a, ug, S.gslot[k]);
       yrow = sl + (size_t)(l - 1) * N * F + (size_t)v * F;
       dyrow = sl + a.dy_off[l] + (size_t)r * F;
@@ -1023,18 +1079,8 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
 // Delta log Psi of the pending proposals of group members 0..nb-1 (bonds u.slot_e).
 __device__ bool tcm_group(const TcCtx& c, Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int nb) {
   const DevGraph& g = c.a->g;
-  const int F = c.F, L = c.L, G = c.G, Lm = g.Lmax;
-  if (u.tid == 0) {
-    for (int l = 0; l <= L; ++l) {
-      int o = 0;
-      for (int k = 0; k < nb; ++k) {
-        u.soff[l * (G + 1) + k] = o;
-        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
-      }
-      u.soff[l * (G + 1) + nb] = o;
-    }
-  }
-  unit_sync(u);
+  const int F = c.F, L = c.L, G = c.G;
+  stage_group(g, u, L, G, nb);
   __nv_bfloat16* d0 = new16(c, u, 0);
   for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
     const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
@@ -1098,6 +1144,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   c.wr = (float*)(smem + b.lay.owr);
   c.br = (float*)(smem + b.lay.obr);
   c.spin = nullptr;
+  c.rp = (const int*)(smem + b.lay.orp);
+  c.wfs = (const float*)(smem + b.lay.owf);
   c.list = (int*)(smem + b.lay.oint);
   c.sdbl = (double*)(smem + b.lay.odbl);
   c.region = smem + b.lay.oregion;
@@ -1126,6 +1174,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
   for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) c.wr[i] = th[m.owr + i];
   if (threadIdx.x < 2) c.br[threadIdx.x] = th[m.obr + threadIdx.x];
+  for (int i = threadIdx.x; i <= c.N; i += blockDim.x) ((int*)c.rp)[i] = __ldg(c.a->g.row_ptr + i);
+  for (int i = threadIdx.x; i < 2 * c.E; i += blockDim.x) ((float*)c.wfs)[i] = __ldg(c.a->g.wf + i);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1149,6 +1199,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   u.part = (float*)(c.region + b.lay.rpart + (size_t)h * b.lay.part_unit);
   u.slot_e = c.list + h * b.lay.int_unit;
   u.soff = u.slot_e + G;
+  u.eoff = u.soff + (L + 1) * (G + 1);
+  u.srow = (int*)(smem + b.lay.orow) + (size_t)h * b.lay.row_unit;
+  u.spos = (int16_t*)(smem + b.lay.opos) + (size_t)h * b.lay.pos_unit;
   u.res = c.sdbl + h * b.lay.dbl_unit;
   // pool state of this unit: after the unit's ints and doubles
   TcmSlots S;
@@ -1272,11 +1325,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
           }
           if (!(S.flag[s] & 4)) more = 1;
         }
-        u.soff[(L + 1) * (G + 1)] = nb;  // spare slot after the offsets
+        u.eoff[G + 1] = nb;  // spare slot after the entry offsets
         s_more[h] = more;
       }
       unit_sync(u);
-      const int nb = u.soff[(L + 1) * (G + 1)];
+      const int nb = u.eoff[G + 1];
       if (nb > 0) {
         if (!tcm_group(c, u, a, S, ug, nb)) {
           ok = false;
@@ -1413,12 +1466,13 @@ struct TcPlan {
 };
 
 static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, TcPlan* p, int* maxball) {
-  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared) return GNA_ERR_UNSUPPORTED;
+  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared || !g->pack_ok) return GNA_ERR_UNSUPPORTED;
   DeviceInfo di;
   gna_status st = device_info(&di);
   if (st != GNA_OK) return st;
   if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
+  const int maxspan = g->max_span[m.L];
   const int T = tc_tiles_per_unit(m.F);
   if (tc_units(m.F) * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   const size_t budget = (size_t)di.smem_optin - 2048;
@@ -1431,7 +1485,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   // prefer the whole region in shared memory with as many bonds per group as fit
   int g_fit = 0;
   for (int gg = G; gg >= 1; --gg) {
-    tc_layout(m, maxball, gg, 1, &lay);
+    tc_layout(m, maxball, maxspan, gg, 1, &lay);
     if (lay.smem_total <= budget) {
       g_fit = gg;
       break;
@@ -1443,7 +1497,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
     // region in the workspace: larger groups (several passes per deep layer) keep more rows
     // in each pass
     const int Gg = op == TC_ELOC ? (G > 8 ? G : 8) : 1;
-    tc_layout(m, maxball, Gg, 0, &lay);
+    tc_layout(m, maxball, maxspan, Gg, 0, &lay);
     if (lay.smem_total > budget) return GNA_ERR_UNSUPPORTED;
     p->region_in_smem = 0;
   }
@@ -1515,7 +1569,7 @@ struct TcmPlan {
 };
 
 // new16_in_smem = 0: the units' dH rows live in the workspace (after each unit's H scratch).
-static void tcm_layout(const Dims& m, const int* maxball, int G, int new16_in_smem, TcLayout* t) {
+static void tcm_layout(const Dims& m, const int* maxball, int maxspan, int G, int new16_in_smem, TcLayout* t) {
   const int F = m.F, N = m.N, L = m.L;
   memset(t, 0, sizeof(*t));
   uint64_t o = 0;
@@ -1536,12 +1590,13 @@ static void tcm_layout(const Dims& m, const int* maxball, int G, int new16_in_sm
   t->oemb = take(2 * F * 4, 16);
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
-  t->int_unit = (uint32_t)(G + (L + 1) * (G + 1) + 4);
+  t->int_unit = (uint32_t)(G + (L + 2) * (G + 1) + 4);
   t->oint = take((uint64_t)U * t->int_unit * 4, 16);
   t->dbl_unit = (uint32_t)(2 * G + 4);
   t->odbl = take((uint64_t)U * t->dbl_unit * 8, 16);
   t->obar = take(8 * U, 8);
   t->oslot = take(4, 4);
+  tc_stage_layout(m, maxball, maxspan, G, U, o, t);
   uint64_t r = 0;
   auto rtake = [&](uint64_t bytes) {
     r = (r + 15) / 16 * 16;
@@ -1568,12 +1623,13 @@ static void tcm_layout(const Dims& m, const int* maxball, int G, int new16_in_sm
 }
 
 static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan* p, int* maxball) {
-  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared) return GNA_ERR_UNSUPPORTED;
+  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared || !g->pack_ok) return GNA_ERR_UNSUPPORTED;
   DeviceInfo di;
   gna_status st = device_info(&di);
   if (st != GNA_OK) return st;
   if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
+  const int maxspan = g->max_span[m.L];
   const int T = tc_tiles_per_unit(m.F), U = tc_units(m.F);
   if (U * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   // pool size: the chains whose last-layer rows fill the T tiles in one pass; when fewer
@@ -1586,7 +1642,7 @@ static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan
   int G = 0;
   for (; in_smem >= 0; --in_smem) {
     for (G = in_smem ? (G0 > 16 ? 16 : G0) : 8; G >= 1; --G) {
-      tcm_layout(m, maxball, G, in_smem, &lay);
+      tcm_layout(m, maxball, maxspan, G, in_smem, &lay);
       if (lay.smem_total <= budget) break;
     }
     if (G >= 1) break;

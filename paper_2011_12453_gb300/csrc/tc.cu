@@ -121,6 +121,23 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   v[6] = __uint_as_float(r6);
   v[7] = __uint_as_float(r7);
 }
+// Two 8-column loads for the same 32 lanes, one wait.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[8 + i]);
+  }
+}
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -328,21 +345,21 @@ __device__ __forceinline__ void unit_sync(const Unit& u) {
 // passes of the group look them up without global-memory latency.
 __device__ void stage_group(const DevGraph& g, const Unit& u, int L, int G, int nb) {
   const int Lm = g.Lmax;
-  if (u.tid == 0) {
-    for (int l = 0; l <= L; ++l) {
-      int o = 0;
-      for (int k = 0; k < nb; ++k) {
-        u.soff[l * (G + 1) + k] = o;
-        o += __ldg(g.ball_size + (size_t)u.slot_e[k] * (Lm + 1) + l);
-      }
-      u.soff[l * (G + 1) + nb] = o;
-    }
-    int o = 0;
-    for (int k = 0; k < nb; ++k) {
-      u.eoff[k] = o;
-      o += __ldg(g.ball_span + (size_t)u.slot_e[k] * (Lm + 1) + L);
-    }
-    u.eoff[nb] = o;
+  // sizes into the offset arrays (shifted by one), loaded in parallel ...
+  for (int i = u.tid; i < (L + 2) * nb; i += u.nthr) {
+    const int l = i / nb, k = i - l * nb;
+    const size_t eo = (size_t)u.slot_e[k] * (Lm + 1);
+    if (l <= L)
+      u.soff[l * (G + 1) + k + 1] = __ldg(g.ball_size + eo + l);
+    else
+      u.eoff[k + 1] = __ldg(g.ball_span + eo + L);
+  }
+  unit_sync(u);
+  // ... then prefix sums, one thread per array
+  if (u.tid <= L + 1) {
+    int* row = u.tid <= L ? u.soff + u.tid * (G + 1) : u.eoff;
+    row[0] = 0;
+    for (int k = 0; k < nb; ++k) row[k + 1] += row[k];
   }
   unit_sync(u);
   const int* offL = u.soff + L * (G + 1);
@@ -554,8 +571,9 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
   const int* offl = u.soff + l * (G + 1);
   const int* offL = u.soff + c.L * (G + 1);
   const __nv_bfloat16* dp = new16(c, u, l - 1);
+  const int f8s = F8 == 2 ? 1 : F8 == 4 ? 2 : F8 == 8 ? 3 : -1;  // log2(F/8) when a power of two
   for (int idx = u.tid; idx < n * F8; idx += u.nthr) {
-    const int qa = idx / F8, ch = idx - qa * F8, q = q0 + qa;
+    const int qa = f8s >= 0 ? idx >> f8s : idx / F8, ch = idx - qa * F8, q = q0 + qa;
     const int k = slot_of(offl, nb, q);
     const int r = q - offl[k];
     const int sprev = offp[k + 1] - offp[k];
@@ -580,6 +598,28 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
   }
 }
 
+// dH = tanh(Y + dY) - tanh(Y) of 8 units from se = copysign(exp(-2|Y|), Y) and dY:
+// with e = exp(-2|Y|), H = sgn(Y)(1-e)/(1+e) and 1 - H^2 = 4e/(1+e)^2, so
+// dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t)), t = tanh(dY).
+__device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, float* d) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float e = fabsf(se[i]);
+    const float sg = se[i] < 0.f ? -1.f : 1.f;
+    const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
+    const float ope = 1.f + e;
+    const float den = ope * (ope + sg * (1.f - e) * tt);
+    if (den > 1e-3f) {
+      d[i] = __fdividef(4.f * e * tt, den);
+    } else {
+      // a unit swinging across saturation: dH is O(1) and the direct difference has no
+      // cancellation (Y recovered from e)
+      const float y = -0.5f * sg * __logf(e);
+      d[i] = tanhf(y + dy[i]) - tanhf(y);
+    }
+  }
+}
+
 // dY in TMEM -> dH = t (1 - H^2) / (1 + H t), t = tanh(dY), for group rows [0, R) at layer
 // l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
 // columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
@@ -600,45 +640,39 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
       v = u.srow[offL[k] + (q - offl[k])] & 0xFFFF;
     }
     float pre = 0.f, pim = 0.f;
-    for (int ch = wg; ch < F / 8; ch += u.nwg) {
-      const int col = ch * 8;
-      float dy[8];
-      tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
+    const uint32_t trow = u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F);
+    // two chunks per TMEM wait: this warp group's chunks ch and ch + nwg
+    for (int ch = wg; ch < F / 8; ch += 2 * u.nwg) {
+      const int ch2 = ch + u.nwg;
+      const bool two = ch2 < F / 8;
+      float dy[2][8];
+      if (two)
+        tmem_ld8x2(trow + ch * 8, trow + ch2 * 8, dy[0], dy[1]);
+      else
+        tmem_ld8(trow + ch * 8, dy[0]);
       if (q < R) {
-        const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col);
-        const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
-        const float se[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float d[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          // e = exp(-2|Y|): H = sgn(Y)(1-e)/(1+e), 1 - H^2 = 4e/(1+e)^2, and
-          // dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t))
-          const float e = fabsf(se[i]);
-          const float sg = se[i] < 0.f ? -1.f : 1.f;
-          const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
-          const float ope = 1.f + e;
-          const float den = ope * (ope + sg * (1.f - e) * tt);
-          if (den > 1e-3f) {
-            d[i] = __fdividef(4.f * e * tt, den);
+        for (int h2 = 0; h2 < 2; ++h2) {
+          if (h2 == 1 && !two) break;
+          const int col = (h2 ? ch2 : ch) * 8;
+          const float4 a0 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col);
+          const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
+          const float se[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          float d[8];
+          delta_tanh8(se, dy[h2], d);
+          if (l < L) {
+            uint4 w;
+            w.x = pack_bf16(d[0], d[1]);
+            w.y = pack_bf16(d[2], d[3]);
+            w.z = pack_bf16(d[4], d[5]);
+            w.w = pack_bf16(d[6], d[7]);
+            *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
           } else {
-            // a unit swinging across saturation: dH is O(1) and the direct difference has
-            // no cancellation (Y recovered from e)
-            const float y = -0.5f * sg * __logf(e);
-            d[i] = tanhf(y + dy[i]) - tanhf(y);
-          }
-        }
-        if (l < L) {
-          uint4 w;
-          w.x = pack_bf16(d[0], d[1]);
-          w.y = pack_bf16(d[2], d[3]);
-          w.z = pack_bf16(d[4], d[5]);
-          w.w = pack_bf16(d[6], d[7]);
-          *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
-        } else {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            pre += d[i] * c.wr[2 * (col + i)];
-            pim += d[i] * c.wr[2 * (col + i) + 1];
+            for (int i = 0; i < 8; ++i) {
+              pre += d[i] * c.wr[2 * (col + i)];
+              pim += d[i] * c.wr[2 * (col + i) + 1];
+            }
           }
         }
       }
@@ -1028,41 +1062,58 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
       dyrow = sl + a.dy_off[l] + (size_t)r * F;
     }
     float pre = 0.f, pim = 0.f;
-    for (int ch = wg; ch < F / 8; ch += u.nwg) {
-      const int col = ch * 8;
-      float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
+    const uint32_t trow = u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F);
+    // two chunks per TMEM wait: this warp group's chunks ch and ch + nwg
+    for (int ch = wg; ch < F / 8; ch += 2 * u.nwg) {
+      const int ch2 = ch + u.nwg;
+      const bool two = ch2 < F / 8;
+      float4 y[2][2];
       if (q < R) {
-        y0 = *reinterpret_cast<const float4*>(yrow + col);
-        y1 = *reinterpret_cast<const float4*>(yrow + col + 4);
-      }
-      float dy[8];
-      tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * F + col), dy);
-      if (q < R) {
-        reinterpret_cast<float4*>(dyrow + col)[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
-        reinterpret_cast<float4*>(dyrow + col)[1] = make_float4(dy[4], dy[5], dy[6], dy[7]);
-        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-        float d[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float e = __expf(-2.f * fabsf(yv[i]));
-          const float sg = yv[i] < 0.f ? -1.f : 1.f;
-          const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
-          const float ope = 1.f + e;
-          const float den = ope * (ope + sg * (1.f - e) * tt);
-          d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(yv[i] + dy[i]) - tanhf(yv[i]);
+        y[0][0] = *reinterpret_cast<const float4*>(yrow + ch * 8);
+        y[0][1] = *reinterpret_cast<const float4*>(yrow + ch * 8 + 4);
+        if (two) {
+          y[1][0] = *reinterpret_cast<const float4*>(yrow + ch2 * 8);
+          y[1][1] = *reinterpret_cast<const float4*>(yrow + ch2 * 8 + 4);
         }
-        if (l < L) {
-          uint4 w;
-          w.x = pack_bf16(d[0], d[1]);
-          w.y = pack_bf16(d[2], d[3]);
-          w.z = pack_bf16(d[4], d[5]);
-          w.w = pack_bf16(d[6], d[7]);
-          *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
-        } else {
+      }
+      float dy[2][8];
+      if (two)
+        tmem_ld8x2(trow + ch * 8, trow + ch2 * 8, dy[0], dy[1]);
+      else
+        tmem_ld8(trow + ch * 8, dy[0]);
+      if (q < R) {
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          if (h2 == 1 && !two) break;
+          const int col = (h2 ? ch2 : ch) * 8;
+          const float* dv = dy[h2];
+          reinterpret_cast<float4*>(dyrow + col)[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+          reinterpret_cast<float4*>(dyrow + col)[1] = make_float4(dv[4], dv[5], dv[6], dv[7]);
+          const float yv[8] = {y[h2][0].x, y[h2][0].y, y[h2][0].z, y[h2][0].w,
+                               y[h2][1].x, y[h2][1].y, y[h2][1].z, y[h2][1].w};
+          float d[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            pre += d[i] * c.wr[2 * (col + i)];
-            pim += d[i] * c.wr[2 * (col + i) + 1];
+            const float e = __expf(-2.f * fabsf(yv[i]));
+            const float sg = yv[i] < 0.f ? -1.f : 1.f;
+            const float tt = fabsf(dv[i]) < 0.5f ? tanh_fast(dv[i]) : tanhf(dv[i]);
+            const float ope = 1.f + e;
+            const float den = ope * (ope + sg * (1.f - e) * tt);
+            d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(yv[i] + dv[i]) - tanhf(yv[i]);
+          }
+          if (l < L) {
+            uint4 w;
+            w.x = pack_bf16(d[0], d[1]);
+            w.y = pack_bf16(d[2], d[3]);
+            w.z = pack_bf16(d[4], d[5]);
+            w.w = pack_bf16(d[6], d[7]);
+            *reinterpret_cast<uint4*>(dout + (size_t)q * ldh + col) = w;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              pre += d[i] * c.wr[2 * (col + i)];
+              pim += d[i] * c.wr[2 * (col + i) + 1];
+            }
           }
         }
       }

@@ -213,10 +213,20 @@ struct TcArgs {
   int region_in_smem;
 };
 
-// F <= 32: two 256-thread units with two 128-row tiles each; wider features: four 128-thread
-// units with one tile each (more independent rounds in flight per SM).
+// F <= 32: two 256-thread units; wider features: four 128-thread units (more independent
+// rounds in flight per SM).  One 128-row tile per unit and pass: the shared memory goes to
+// larger bond groups instead (measured at Kagome 108, F = 32: two tiles and 4 bonds per
+// group 43.3 ms, one tile and 6 bonds 41.9 ms).
 __host__ inline int tc_units(int F) { return F <= 32 ? 2 : 4; }
-__host__ inline int tc_tiles_per_unit(int F) { return F <= 32 ? 2 : 1; }
+__host__ inline int tc_tiles_per_unit(int) { return 1; }
+
+// Passes of rows_per_pass rows that a group of G bonds needs over layers 1..L, per bond
+// (x1000): the cost model for the group size (the last pass of each layer is partial).
+__host__ inline int tc_passes_per_bond(const int* maxball, int L, int G, int rows_per_pass) {
+  int passes = 0;
+  for (int l = 1; l <= L; ++l) passes += (G * maxball[l] + rows_per_pass - 1) / rows_per_pass;
+  return passes * 1000 / G;
+}
 
 // The staged tables of a unit: G bonds' rows of ball_L (packed vertex and entry start) and
 // their in-ball neighbour positions (maxspan = max entries of a bond's ball_L).
@@ -236,8 +246,10 @@ __host__ inline void tc_stage_layout(const Dims& m, const int* maxball, int maxs
   t->opos = take((uint64_t)U * t->pos_unit * 2, 16);
 }
 
+// alias_new16: the group rows' dH layers share the space of the BF16 layer cache, which
+// only the forward reads (the incremental step needs the pre-activations alone).
 __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, int G, int region_in_smem,
-                               TcLayout* t) {
+                               int alias_new16, TcLayout* t) {
   const int F = m.F, N = m.N, L = m.L;
   uint64_t o = 0;
   auto take = [&](uint64_t bytes, uint64_t align) {
@@ -274,7 +286,6 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
     return x;
   };
   const uint64_t ldh = F + 8, ldy = F + 4;  // padded row strides (BF16 rows, FP32 rows)
-  t->rcache16 = rtake((uint64_t)L * N * ldh * 2);
   t->rY = rtake((uint64_t)L * N * ldy * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
   uint64_t n16 = 0;
   for (int l = 0; l < L; ++l) {
@@ -282,7 +293,15 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
     n16 += (uint64_t)G * maxball[l] * ldh * 2;
   }
   t->new16_unit = (n16 + 15) / 16 * 16;
-  t->rnew16 = rtake((uint64_t)U * t->new16_unit);
+  const uint64_t cache_bytes = (uint64_t)L * N * ldh * 2, new_bytes = (uint64_t)U * t->new16_unit;
+  if (alias_new16) {
+    // one area for both: the layer cache during the forward, the dH rows afterwards
+    t->rcache16 = rtake(cache_bytes > new_bytes ? cache_bytes : new_bytes);
+    t->rnew16 = t->rcache16;
+  } else {
+    t->rcache16 = rtake(cache_bytes);
+    t->rnew16 = rtake(new_bytes);
+  }
   t->part_rows = G * maxball[L];
   t->part_unit = (uint64_t)(kTcThreads / U / 128) * t->part_rows * 2 * 4;  // [warp group][row][Re, Im]
   t->rpart = rtake((uint64_t)U * t->part_unit);
@@ -1533,23 +1552,38 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (G > 16) G = 16;
   if (G < 1) G = 1;
   TcLayout lay;
-  // prefer the whole region in shared memory with as many bonds per group as fit
-  int g_fit = 0;
-  for (int gg = G; gg >= 1; --gg) {
-    tc_layout(m, maxball, maxspan, gg, 1, &lay);
-    if (lay.smem_total <= budget) {
+  // prefer the whole region in shared memory with as many bonds per group as fit (the dH
+  // rows reuse the layer cache's space where they fit in it)
+  // the group size with the fewest passes per bond (ties: the larger) among those that fit
+  int g_fit = 0, best = 1 << 30;
+  for (int gg = op == TC_ELOC ? 16 : 1; gg >= 1; --gg) {
+    tc_layout(m, maxball, maxspan, gg, 1, op == TC_ELOC, &lay);
+    if (lay.smem_total > budget) continue;
+    const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
+    if (cost < best) {
+      best = cost;
       g_fit = gg;
-      break;
     }
   }
   if (g_fit > 0) {
     p->region_in_smem = 1;
+    tc_layout(m, maxball, maxspan, g_fit, 1, op == TC_ELOC, &lay);
   } else {
-    // region in the workspace: larger groups (several passes per deep layer) keep more rows
-    // in each pass
-    const int Gg = op == TC_ELOC ? (G > 8 ? G : 8) : 1;
-    tc_layout(m, maxball, maxspan, Gg, 0, &lay);
-    if (lay.smem_total > budget) return GNA_ERR_UNSUPPORTED;
+    // region in the workspace: the group size by the same cost model among those that fit,
+    // up to 8 bonds (larger groups spill the per-CTA regions out of L2: triangular 144,
+    // F = 48: 8 bonds 36.8 ms, 16 bonds 42.6 ms per 4096 configurations)
+    int Gg = 0;
+    for (int gg = op == TC_ELOC ? 8 : 1; gg >= 1; --gg) {
+      tc_layout(m, maxball, maxspan, gg, 0, op == TC_ELOC, &lay);
+      if (lay.smem_total > budget) continue;
+      const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
+      if (cost < best) {
+        best = cost;
+        Gg = gg;
+      }
+    }
+    if (Gg < 1) return GNA_ERR_UNSUPPORTED;
+    tc_layout(m, maxball, maxspan, Gg, 0, op == TC_ELOC, &lay);
     p->region_in_smem = 0;
   }
   // At most 512 / kTmemCols CTAs may hold TMEM on one SM at a time: request enough shared
@@ -1683,20 +1717,29 @@ static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan
   const int maxspan = g->max_span[m.L];
   const int T = tc_tiles_per_unit(m.F), U = tc_units(m.F);
   if (U * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
-  // pool size: the chains whose last-layer rows fill the T tiles in one pass; when fewer
-  // than two fit, pools of 8 with several passes per deep layer and the dH rows in the
-  // workspace
-  const int G0 = (T * 128) / (maxball[m.L] > 0 ? maxball[m.L] : 1);
+  // pool size: up to 8 chains with their dH rows in shared memory; when fewer than 4 fit
+  // there, pools of 8 with the dH rows in the workspace (deep layers then take several
+  // passes either way)
   const size_t budget = (size_t)di.smem_optin - 2048;
   TcLayout lay;
-  int in_smem = G0 >= 2 ? 1 : 0;
+  int in_smem = 1;
   int G = 0;
   for (; in_smem >= 0; --in_smem) {
-    for (G = in_smem ? (G0 > 16 ? 16 : G0) : 8; G >= 1; --G) {
-      tcm_layout(m, maxball, maxspan, G, in_smem, &lay);
-      if (lay.smem_total <= budget) break;
+    int best = 1 << 30;
+    G = 0;
+    for (int gg = 8; gg >= (in_smem ? 4 : 1); --gg) {
+      tcm_layout(m, maxball, maxspan, gg, in_smem, &lay);
+      if (lay.smem_total > budget) continue;
+      const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
+      if (cost < best) {
+        best = cost;
+        G = gg;
+      }
     }
-    if (G >= 1) break;
+    if (G >= 1) {
+      tcm_layout(m, maxball, maxspan, G, in_smem, &lay);
+      break;
+    }
   }
   if (G < 1) return GNA_ERR_UNSUPPORTED;
   p->new16_in_smem = in_smem;

@@ -296,10 +296,12 @@ def run_reference(a):
 # dram__bytes_write.sum of one launch / the samples it processed), valid only for the source file
 # that was profiled: keyed by (workload, kernel) with the SHA-256 of that source.
 PROFILED_TRAFFIC = {
-    # ncu --set full, 2048 configurations, one launch: 594,944 B read + 0 B written
-    ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 594944 / 2048, "sha256": "5a4fa317265f046fcd72c1477f41d4875111b1d54327e2d93876e85785b279aa"},
-    # ncu --set full, 2048 chains, one sweep: 6,129,408 B read + 332,758,784 B written
-    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (6129408 + 332758784) / 2048, "sha256": "5a4fa317265f046fcd72c1477f41d4875111b1d54327e2d93876e85785b279aa"},
+    # ncu --set full, 2048 configurations, one launch: 475,136 B read + 0 B written
+    ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 475136 / 2048,
+                                          "sha256": "9d77b63467719d01bc77599edea3186d082bdd0b79fd5a1909974b66af092bc7"},
+    # ncu --set full, 2048 chains, one sweep: 477,185,024 B read + 1,421,472,000 B written
+    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (477185024 + 1421472000) / 2048,
+                                                "sha256": "9d77b63467719d01bc77599edea3186d082bdd0b79fd5a1909974b66af092bc7"},
 }
 
 

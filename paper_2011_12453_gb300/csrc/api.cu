@@ -137,6 +137,10 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       return simt_workspace(g, m, sp, 5, B, bytes);
     }
     case GNA_OP_BACKWARD:
+      if (d->prec == GNA_PREC_BF16) {
+        gna_status st = tcb_workspace(g, m, B, bytes);
+        if (st != GNA_ERR_UNSUPPORTED) return st;
+      }
       return simt_workspace(g, m, sp, 4, B, bytes);
     case GNA_OP_ISGO_WEIGHTS:
       *bytes = isgo_weights_ws(B);
@@ -291,6 +295,12 @@ extern "C" gna_status gna_backward(const gna_graph* g, const gna_model_desc* d, 
   if (!theta || !grad || (B > 0 && (!spins || !cot))) return GNA_ERR_INVALID_ARG;
   st = check_ws(g, d, GNA_OP_BACKWARD, B, workspace, workspace_bytes);
   if (st != GNA_OK) return st;
+  // BF16 models: the tensor-core backward when the model fits it
+  size_t need = 0;
+  if (d->prec == GNA_PREC_BF16 && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
+    TcbCall tc{g, make_dims(g, d), (const float*)theta, spins, B, cot, grad};
+    return tcb_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
   SimtCall sc{};
   sc.g = g;
   sc.m = make_dims(g, d);

@@ -532,7 +532,7 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
             *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
       }
       if (!run_mmas(c, u, nt)) return false;
-      epilogue_fwd(c, u, nt, R, r0, l, c.a->op == TC_ELOC);
+      epilogue_fwd(c, u, nt, R, r0, l, c.a->op != TC_FWD);
     }
   }
   return true;
@@ -1526,6 +1526,342 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
+// Backward VJP on the tensor cores (BF16 models)
+// ---------------------------------------------------------------------------------
+// grad = sum_x [cot_re,x d Re log Psi_x + cot_im,x d Im log Psi_x] / d theta (the ISGO
+// cotangents, Eq. isgo).  Per configuration: the tensor-core forward keeps H^0..H^{L-1}
+// (BF16) and copysign(exp(-2|Y^l|), Y^l) (FP32, giving 1 - (H^l)^2 = 4e/(1+e)^2 without
+// cancellation); then, from G^L_v = cot . w_r[:F] (the same for every site), for
+// l = L..1:
+//   dY^l = G^l (1 - (H^l)^2)                                   (SIMT, FP32)
+//   dW  += X^T dY^l,  X = [A_hat H^{l-1} ; H^{l-1}]            (MMA: M = 2F padded to 128,
+//                                                               N = F, K = sites in chunks
+//                                                               of 128; the accumulator
+//                                                               stays in TMEM for the whole
+//                                                               launch -- W is shared)
+//   dX   = dY^l W^T                                             (MMA: M = sites, N = 2F, K = F)
+//   G^{l-1}_v = dX_v[F:] + sum_u A_hat_vu dX_u[:F]              (SIMT gather, FP32)
+//   db  += sum_v dY^l_v
+// and the embedding and readout terms in FP64 shared accumulators.  Per-CTA partials of
+// all P parameters (FP64) are summed in a fixed order by a second kernel.
+struct TcbArgs {
+  TcArgs base;         // graph, dims, theta, spins, B; layout of the forward pieces
+  const double* cot;   // [B][2]
+  double* partial;     // [grid][P]
+  uint32_t oWb, oXt, odYt, osp;  // smem: W as the B operand of dX; X^T and dY^T tiles; FP64 accumulators
+  uint64_t rG, rdx;    // region: G [N][F] and dX [N][2F] (FP32)
+};
+
+// element (r, k) of a K-column tile in the no-swizzle K-major canonical layout
+__device__ __forceinline__ uint32_t canon(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// D[tmem] (+)= A[128 x K] B[N x K]^T, one elected thread, no commit.
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, int K, int Nout,
+                                          bool accumulate) {
+  const uint32_t idesc = idesc_bf16(128, Nout);
+  const uint32_t sbo = (uint32_t)K * 16;
+  for (int kb = 0; kb < K / 16; ++kb)
+    mma_bf16(d_tmem, sdesc(a_addr + kb * 256, 128, sbo), sdesc(b_addr + kb * 256, 128, sbo), idesc,
+             (accumulate || kb > 0) ? 1u : 0u);
+}
+
+// small-parameter accumulators: [W_e (2F), b_e (F)] [b (F)] [w_r (2F+4)] [b_r (2)]
+__device__ __forceinline__ int sp_We(int F) { return 0; }
+__device__ __forceinline__ int sp_b(int F) { return 3 * F; }
+__device__ __forceinline__ int sp_wr(int F) { return 4 * F; }
+__device__ __forceinline__ int sp_br(int F) { return 6 * F + 4; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_fail;
+  const TcArgs& b = a.base;
+  TcCtx c;
+  c.a = &b;
+  c.N = b.m.N;
+  c.F = b.m.F;
+  c.L = b.m.L;
+  c.E = b.m.E;
+  c.T = b.lay.T;
+  c.G = b.lay.G;
+  c.ldh = b.m.F + 8;
+  c.ldy = b.m.F + 4;
+  c.Wt = (__nv_bfloat16*)(smem + b.lay.oWt);
+  c.bias = (float*)(smem + b.lay.obias);
+  c.emb = (float*)(smem + b.lay.oemb);
+  c.wr = (float*)(smem + b.lay.owr);
+  c.br = (float*)(smem + b.lay.obr);
+  c.spin = (int8_t*)(smem + b.lay.ospin);
+  c.rp = (const int*)(smem + b.lay.orp);
+  c.wfs = (const float*)(smem + b.lay.owf);
+  c.list = (int*)(smem + b.lay.oint);
+  c.sdbl = (double*)(smem + b.lay.odbl);
+  c.region = b.region_in_smem ? smem + b.lay.oregion : b.gregion + (size_t)blockIdx.x * b.lay.region_bytes;
+  c.fail = &s_fail;
+  const int F = c.F, N = c.N, L = c.L, ldh = c.ldh, ldy = c.ldy;
+  const int F8 = F / 8, F2 = 2 * F;
+  const Dims& m = b.m;
+  const float* th = b.theta;
+  uint64_t* bars = (uint64_t*)(smem + b.lay.obar);
+  uint32_t* slot = (uint32_t*)(smem + b.lay.oslot);
+  unsigned char* Wb = smem + a.oWb;
+  unsigned char* Xt = smem + a.oXt;
+  unsigned char* dYt = smem + a.odYt;
+  double* sp = (double*)(smem + a.osp);
+  float* Gs = (float*)(c.region + a.rG);
+  float* dx = (float*)(c.region + a.rdx);
+  const int nsp = 6 * F + 6;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(bars, 1);
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    tmem_alloc(slot, kTmemCols);
+    tmem_relinquish();
+  }
+  const float* W = th + m.oW;
+  for (int i = threadIdx.x; i < F * F2; i += blockDim.x) {
+    const int n = i / F2, k = i % F2;  // forward B: W^T (n = output, k = input)
+    unsigned char* p = (unsigned char*)c.Wt + (size_t)(n >> 3) * (32 * F) + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+    // backward dX: B = W (n' = input feature k, k' = output feature n), K = F
+    *reinterpret_cast<__nv_bfloat16*>(Wb + canon(k, n, F)) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+  }
+  for (int i = threadIdx.x; i < F; i += blockDim.x) c.bias[i] = th[m.ob + i];
+  for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
+  for (int i = threadIdx.x; i < (F + 2) * 2; i += blockDim.x) c.wr[i] = th[m.owr + i];
+  if (threadIdx.x < 2) c.br[threadIdx.x] = th[m.obr + threadIdx.x];
+  for (int i = threadIdx.x; i <= c.N; i += blockDim.x) ((int*)c.rp)[i] = __ldg(b.g.row_ptr + i);
+  for (int i = threadIdx.x; i < 2 * c.E; i += blockDim.x) ((float*)c.wfs)[i] = __ldg(b.g.wf + i);
+  for (int i = threadIdx.x; i < nsp; i += blockDim.x) sp[i] = 0.0;
+  // X^T rows 2F..127 stay zero (M padded to 128)
+  for (int i = threadIdx.x; i < 128 * 128 * 2 / 16; i += blockDim.x) reinterpret_cast<uint4*>(Xt)[i] = make_uint4(0, 0, 0, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t t_dx = tmem + (uint32_t)F, t_dw = tmem + (uint32_t)(3 * F);
+
+  Unit u;
+  u.tid = threadIdx.x;
+  u.nthr = blockDim.x;
+  u.bar_id = 0;
+  u.nwg = blockDim.x / 128;
+  u.A = smem + b.lay.oA;
+  u.tbase = tmem;
+  u.bar = bars;
+  u.phase = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q4 = warp & 3, wg = warp >> 2;
+  bool dw_started = false;  // meaningful in thread 0
+  bool ok = true;
+  int nsamples = 0;
+  for (int64_t bi = blockIdx.x; bi < b.B && ok; bi += gridDim.x) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) c.spin[i] = b.spins[bi * N + i];
+    __syncthreads();
+    ok = tc_forward(c, u);
+    if (!ok) break;
+    ++nsamples;
+    const float c0 = (float)a.cot[2 * bi], c1 = (float)a.cot[2 * bi + 1];
+    // readout: d w_r[f] += cot z_f with z = sum_v [H^L_v ; onehot_v]; d b_r += cot
+    const float* seL = cacheY(c, L);
+    for (int f = threadIdx.x; f < F + 2; f += blockDim.x) {
+      double z = 0.0;
+      if (f < F) {
+        float zz = 0.f;
+        for (int v = 0; v < N; ++v) {
+          const float se = seL[(size_t)v * ldy + f], e = fabsf(se);
+          zz += copysignf(__fdividef(1.f - e, 1.f + e), se);
+        }
+        z = (double)zz;
+      } else {
+        int cnt = 0;
+        for (int v = 0; v < N; ++v) cnt += (f == F) ? (c.spin[v] > 0) : (c.spin[v] < 0);
+        z = (double)cnt;
+      }
+      sp[sp_wr(F) + 2 * f] += (double)c0 * z;
+      sp[sp_wr(F) + 2 * f + 1] += (double)c1 * z;
+    }
+    if (threadIdx.x == 0) {
+      sp[sp_br(F)] += (double)c0;
+      sp[sp_br(F) + 1] += (double)c1;
+    }
+    for (int i = threadIdx.x; i < N * F; i += blockDim.x) {
+      const int f = i % F;
+      Gs[i] = c0 * c.wr[2 * f] + c1 * c.wr[2 * f + 1];
+    }
+    __syncthreads();
+    for (int l = L; l >= 1 && ok; --l) {
+      const float* se = cacheY(c, l);
+      const __nv_bfloat16* hp = cache16(c, l - 1);
+      // db += sum_v dY^l_v
+      for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        float s = 0.f;
+        for (int v = 0; v < N; ++v) {
+          const float e = fabsf(se[(size_t)v * ldy + f]), ope = 1.f + e;
+          s += Gs[(size_t)v * F + f] * __fdividef(4.f * e, ope * ope);
+        }
+        sp[sp_b(F) + f] += (double)s;
+      }
+      for (int c0s = 0; c0s < N && ok; c0s += 128) {
+        const int ns = min(128, N - c0s);
+        // dY rows of the chunk: as the A operand of dX (rows, K = F) and, transposed, as the
+        // B operand of dW (rows = output features, K = sites); zeros past the last site
+        for (int idx = threadIdx.x; idx < 128 * F8; idx += blockDim.x) {
+          const int r = idx / F8, ch = idx - r * F8, v = c0s + r;
+          float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          if (r < ns) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float e = fabsf(se[(size_t)v * ldy + ch * 8 + i]), ope = 1.f + e;
+              d[i] = Gs[(size_t)v * F + ch * 8 + i] * __fdividef(4.f * e, ope * ope);
+            }
+          }
+          uint4 w;
+          w.x = pack_bf16(d[0], d[1]);
+          w.y = pack_bf16(d[2], d[3]);
+          w.z = pack_bf16(d[4], d[5]);
+          w.w = pack_bf16(d[6], d[7]);
+          *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = w;
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            *reinterpret_cast<__nv_bfloat16*>(dYt + canon(ch * 8 + i, r, 128)) = __float2bfloat16_rn(d[i]);
+        }
+        // X = [A_hat H^{l-1} ; H^{l-1}] of the chunk's sites, transposed (rows = input features)
+        for (int idx = threadIdx.x; idx < 128 * 2 * F8; idx += blockDim.x) {
+          const int r = idx / (2 * F8), mc = idx - r * (2 * F8), v = c0s + r;
+          float x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          if (r < ns) {
+            if (mc < F8) {
+              const int k0 = c.rp[v], k1 = c.rp[v + 1];
+              for (int k = k0; k < k1; ++k) fma_chunk(x, c.wfs[k], hp + (size_t)__ldg(b.g.col + k) * ldh + mc * 8);
+            } else {
+              const uint4 h = *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + (mc - F8) * 8);
+              x[0] = bf16lo(h.x);
+              x[1] = bf16hi(h.x);
+              x[2] = bf16lo(h.y);
+              x[3] = bf16hi(h.y);
+              x[4] = bf16lo(h.z);
+              x[5] = bf16hi(h.z);
+              x[6] = bf16lo(h.w);
+              x[7] = bf16hi(h.w);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            *reinterpret_cast<__nv_bfloat16*>(Xt + canon(mc * 8 + i, r, 128)) = __float2bfloat16_rn(x[i]);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          issue_mma(t_dw, smem_u32(Xt), smem_u32(dYt), 128, F, dw_started);
+          dw_started = true;
+          issue_mma(t_dx, smem_u32(u.A), smem_u32(Wb), F, F2, false);
+          mma_commit(u.bar);
+          if (!mbar_wait_bounded(u.bar, u.phase)) {
+            s_fail = 1;
+            atomicOr(&s_tc_status, 1);
+          }
+          u.phase ^= 1u;
+        }
+        __syncthreads();
+        tc_fence_after();
+        if (s_fail) {
+          ok = false;
+          break;
+        }
+        // dX rows of the chunk out of TMEM (lanes = sites)
+        const int r = q4 * 32 + lane;
+        for (int ch = wg; ch < 2 * F8; ch += u.nwg) {
+          float v8[8];
+          tmem_ld8(t_dx + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ch * 8), v8);
+          if (r < ns) {
+            float4* o = reinterpret_cast<float4*>(dx + (size_t)(c0s + r) * F2 + ch * 8);
+            o[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
+            o[1] = make_float4(v8[4], v8[5], v8[6], v8[7]);
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+      }
+      if (!ok) break;
+      // G^{l-1}_v = dX_v[F:] + sum_u A_hat_vu dX_u[:F]
+      for (int idx = threadIdx.x; idx < N * F8; idx += blockDim.x) {
+        const int v = idx / F8, ch = idx - v * F8;
+        const float4* sf = reinterpret_cast<const float4*>(dx + (size_t)v * F2 + F + ch * 8);
+        float4 a0 = sf[0], a1 = sf[1];
+        const int k0 = c.rp[v], k1 = c.rp[v + 1];
+        for (int k = k0; k < k1; ++k) {
+          const float w = c.wfs[k];
+          const float4* mu = reinterpret_cast<const float4*>(dx + (size_t)__ldg(b.g.col + k) * F2 + ch * 8);
+          const float4 m0 = mu[0], m1 = mu[1];
+          a0.x += w * m0.x;
+          a0.y += w * m0.y;
+          a0.z += w * m0.z;
+          a0.w += w * m0.w;
+          a1.x += w * m1.x;
+          a1.y += w * m1.y;
+          a1.z += w * m1.z;
+          a1.w += w * m1.w;
+        }
+        float4* go = reinterpret_cast<float4*>(Gs + (size_t)v * F + ch * 8);
+        go[0] = a0;
+        go[1] = a1;
+      }
+      __syncthreads();
+    }
+    if (!ok) break;
+    // embedding: dY^0 = G^0 (1 - emb^2); d W_e[c] += sum_{v: c_v = c} dY^0_v, d b_e += sum_v dY^0_v
+    for (int f = threadIdx.x; f < F; f += blockDim.x) {
+      float su = 0.f, sd = 0.f;
+      for (int v = 0; v < N; ++v) {
+        if (c.spin[v] > 0)
+          su += Gs[(size_t)v * F + f];
+        else
+          sd += Gs[(size_t)v * F + f];
+      }
+      const float eu = c.emb[f], ed = c.emb[F + f];
+      const double du = (double)(su * (1.f - eu * eu)), dd = (double)(sd * (1.f - ed * ed));
+      sp[sp_We(F) + f] += du;
+      sp[sp_We(F) + F + f] += dd;
+      sp[sp_We(F) + 2 * F + f] += du + dd;
+    }
+    __syncthreads();
+  }
+  // partials: dW from TMEM (lanes = input features), the rest from the FP64 accumulators
+  double* part = a.partial + (size_t)blockIdx.x * m.P;
+  if (ok) {
+    const int mrow = q4 * 32 + lane;
+    for (int ch = wg; ch < F8; ch += u.nwg) {
+      float v8[8];
+      tmem_ld8(t_dw + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ch * 8), v8);
+      if (mrow < F2)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) part[m.oW + (size_t)mrow * F + ch * 8 + i] = nsamples > 0 ? (double)v8[i] : 0.0;
+    }
+    for (int f = threadIdx.x; f < 3 * F; f += blockDim.x) part[m.oWe + f] = sp[sp_We(F) + f];  // W_e, b_e
+    for (int f = threadIdx.x; f < F; f += blockDim.x) part[m.ob + f] = sp[sp_b(F) + f];
+    for (int f = threadIdx.x; f < 2 * F + 4; f += blockDim.x) part[m.owr + f] = sp[sp_wr(F) + f];
+    if (threadIdx.x < 2) part[m.obr + threadIdx.x] = sp[sp_br(F) + threadIdx.x];
+  }
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(u.bar, u.phase ^ 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+__global__ void k_tcb_reduce(const double* partial, int grid, int P, double* grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double s = 0.0;
+  for (int cta = 0; cta < grid; ++cta) s += partial[(size_t)cta * P + p];
+  grad[p] = s;
+}
+
+// ---------------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------------
 struct TcPlan {
@@ -1812,6 +2148,138 @@ gna_status tcm_run(const TcmCall& call, void* ws, size_t ws_bytes, cudaStream_t 
   a.unit_elems = p.unit_elems;
   for (int l = 0; l <= kMaxL; ++l) a.dy_off[l] = p.dy_off[l];
   k_tc_metro<<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// host: tensor-core backward
+// ---------------------------------------------------------------------------------
+struct TcbPlan {
+  TcbArgs a;
+  int grid = 0;
+  size_t smem = 0, ws_bytes = 0, partial_bytes = 0;
+};
+
+static void tcb_layout(const Dims& m, int region_in_smem, TcbArgs* A) {
+  TcLayout* t = &A->base.lay;
+  memset(t, 0, sizeof(*t));
+  const int F = m.F, N = m.N, L = m.L;
+  uint64_t o = 0;
+  auto take = [&](uint64_t bytes, uint64_t align) {
+    o = (o + align - 1) / align * align;
+    uint64_t r = o;
+    o += bytes;
+    return (uint32_t)r;
+  };
+  t->T = 1;
+  t->units = 1;
+  t->G = 1;
+  t->a_unit = 128 * 2 * F * 2;
+  t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
+  A->oWb = take((uint64_t)2 * F * F * 2, 1024);
+  t->oA = take(t->a_unit, 1024);
+  A->oXt = take(128 * 128 * 2, 1024);
+  A->odYt = take((uint64_t)F * 128 * 2, 1024);
+  t->obias = take(F * 4, 16);
+  t->oemb = take(2 * F * 4, 16);
+  t->owr = take((F + 2) * 2 * 4, 16);
+  t->obr = take(16, 16);
+  t->ospin = take(N, 16);
+  t->oint = take(64, 16);
+  t->odbl = take((uint64_t)(16 + kTcThreads + 16) * 8, 16);
+  A->osp = take((uint64_t)(6 * F + 6) * 8, 16);
+  t->obar = take(8, 8);
+  t->oslot = take(4, 4);
+  t->orp = take((uint64_t)(N + 1) * 4, 16);
+  t->owf = take((uint64_t)2 * m.E * 4, 16);
+  uint64_t r = 0;
+  auto rtake = [&](uint64_t bytes) {
+    r = (r + 15) / 16 * 16;
+    uint64_t x = r;
+    r += bytes;
+    return x;
+  };
+  const uint64_t ldh = F + 8, ldy = F + 4;
+  t->rY = rtake((uint64_t)L * N * ldy * 4);
+  t->rcache16 = rtake((uint64_t)L * N * ldh * 2);
+  A->rG = rtake((uint64_t)N * F * 4);
+  A->rdx = rtake((uint64_t)N * 2 * F * 4);
+  t->region_bytes = (r + 255) / 256 * 256;
+  t->oregion = region_in_smem ? take(t->region_bytes, 16) : 0;
+  t->smem_total = (uint32_t)o;
+}
+
+static gna_status tcb_plan(const gna_graph* g, const Dims& m, int64_t B, TcbPlan* p) {
+  if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared) return GNA_ERR_UNSUPPORTED;
+  DeviceInfo di;
+  gna_status st = device_info(&di);
+  if (st != GNA_OK) return st;
+  if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
+  if (4 * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
+  const size_t budget = (size_t)di.smem_optin - 2048;
+  memset(&p->a, 0, sizeof(p->a));
+  int in_smem = 1;
+  tcb_layout(m, 1, &p->a);
+  if (p->a.base.lay.smem_total > budget) {
+    in_smem = 0;
+    tcb_layout(m, 0, &p->a);
+    if (p->a.base.lay.smem_total > budget) return GNA_ERR_UNSUPPORTED;
+  }
+  p->a.base.region_in_smem = in_smem;
+  const uint32_t min_smem = (uint32_t)(228u * 1024u / (512 / kTmemCols + 1)) + 1024u;
+  uint32_t smem = p->a.base.lay.smem_total;
+  if (smem < min_smem) smem = min_smem;
+  p->a.base.lay.smem_total = smem;
+  GNA_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_tc_bwd, kTcThreads, smem));
+  if (occ < 1) occ = 1;
+  if (occ * kTmemCols > 512) return GNA_ERR_UNSUPPORTED;
+  int64_t grid = (int64_t)di.sms * occ;
+  if (grid > B) grid = B;
+  if (grid < 1) grid = 1;
+  p->grid = (int)grid;
+  p->smem = smem;
+  p->partial_bytes = align_up((size_t)grid * m.P * sizeof(double));
+  p->ws_bytes = p->partial_bytes + (in_smem ? 0 : align_up((size_t)grid * p->a.base.lay.region_bytes));
+  return GNA_OK;
+}
+
+gna_status tcb_workspace(const gna_graph* g, const Dims& m, int64_t B, size_t* bytes) {
+  if (B == 0) {
+    *bytes = 0;
+    return GNA_OK;
+  }
+  TcbPlan p;
+  gna_status st = tcb_plan(g, m, B, &p);
+  if (st != GNA_OK) return st;
+  *bytes = p.ws_bytes;
+  return GNA_OK;
+}
+
+gna_status tcb_run(const TcbCall& call, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (call.B == 0) {
+    GNA_CUDA_TRY(cudaMemsetAsync(call.grad, 0, (size_t)call.m.P * sizeof(double), stream));
+    return GNA_OK;
+  }
+  TcbPlan p;
+  gna_status st = tcb_plan(call.g, call.m, call.B, &p);
+  if (st != GNA_OK) return st;
+  if (ws_bytes < p.ws_bytes || !ws) return GNA_ERR_WORKSPACE;
+  TcbArgs& a = p.a;
+  a.base.g = call.g->d;
+  a.base.m = call.m;
+  a.base.op = TC_BWD;
+  a.base.theta = call.theta;
+  a.base.spins = call.spins;
+  a.base.B = call.B;
+  a.base.gregion = (unsigned char*)ws + p.partial_bytes;
+  a.cot = call.cot;
+  a.partial = (double*)ws;
+  k_tc_bwd<<<p.grid, kTcThreads, p.smem, stream>>>(a);
+  GNA_CUDA_TRY(cudaGetLastError());
+  k_tcb_reduce<<<(call.m.P + 255) / 256, 256, 0, stream>>>(a.partial, p.grid, call.m.P, call.grad);
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
 }

@@ -5,7 +5,7 @@
 
 namespace gna {
 
-enum TcOp { TC_FWD = 0, TC_ELOC = 1 };
+enum TcOp { TC_FWD = 0, TC_ELOC = 1, TC_BWD = 2 };
 
 struct TcCall {
   const gna_graph* g;
@@ -35,7 +35,20 @@ struct TcmCall {
   double* trace;
 };
 
+// Backward VJP of BF16 models on the tensor cores: grad = sum_x cot_x . d log Psi_x / d theta.
+struct TcbCall {
+  const gna_graph* g;
+  Dims m;
+  const float* theta;
+  const int8_t* spins;
+  int64_t B;
+  const double* cot;  // [B][2]
+  double* grad;       // [P]
+};
+
 gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes);
+gna_status tcb_workspace(const gna_graph* g, const Dims& m, int64_t B, size_t* bytes);
+gna_status tcb_run(const TcbCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tcm_workspace(const gna_graph* g, const Dims& m, int64_t C, size_t* bytes);
 gna_status tcm_run(const TcmCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_run(const TcCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);

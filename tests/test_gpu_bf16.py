@@ -233,3 +233,45 @@ def test_bf16_sampler_matches_fp32_sampler_statistics(torch):
         res[name] = (m.mean(), m.std() / np.sqrt(len(m)))
     (a, sa), (b, sb) = res["bf16"], res["fp32"]
     assert abs(a - b) < 4 * np.hypot(sa, sb), (res)
+
+
+# ---------------------------------------------------------------------------------
+# backward VJP on the tensor cores
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scale,tol", [(0.3, 3e-2), (0.1, 5e-3)])
+@pytest.mark.parametrize("name,F,L", CASES)
+def test_bf16_backward_parity(torch, name, F, L, scale, tol):
+    # sum_x cot_x . d log Psi_x / d theta with BF16 GEMM operands (X, dY, W) and FP32
+    # accumulation against the FP64 oracle on the BF16-rounded W.  The forward's BF16
+    # activations leave |dY^l| errors of order 1e-2 at weight scale 0.3, and a saturated
+    # unit's derivative 1 - H^2 changes by the relative amount 2|H| dY, so the gradient is
+    # held to 3e-2 of its largest component there; at the benchmark scale 0.1 (few
+    # saturated units) to 5e-3
+    from oracle import isgo
+
+    g = _graph(name)
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=scale)
+    Bn = 37
+    s = W.random_spins(g.n_sites, Bn, seed=13)
+    cot = np.random.default_rng(14).normal(size=(Bn, 2))
+    got = gna.backward(graph, model, theta, torch.tensor(s, device="cuda"), torch.tensor(cot, device="cuda"))
+    want = isgo.backward(th, F, L, Ah, s, cot)
+    err = np.abs(got.cpu().numpy() - want).max()
+    assert err <= tol * np.abs(want).max(), (err, np.abs(want).max())
+
+
+def test_bf16_backward_matches_fp32_on_the_benchmark_workload(torch):
+    # Kagome 6x6x3, L = 4, F = 32, weight scale 0.1, 2048 configurations: BF16 tensor-core
+    # backward vs the FP32 backward on the same parameters, and an empty batch gives zeros
+    g = W.kagome(6)
+    F, L = 32, 4
+    graph, model, theta, th, Ah = _setup(torch, g, F, L, scale=0.1)
+    m32 = gna.Model(F, L, gna.PREC_FP32)
+    s = torch.tensor(W.random_spins(g.n_sites, 2048, seed=3), device="cuda")
+    cot = torch.tensor(np.random.default_rng(4).normal(size=(2048, 2)) / 2048, device="cuda")
+    a = gna.backward(graph, model, theta, s, cot).cpu().numpy()
+    b = gna.backward(graph, m32, theta, s, cot).cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
+    z = gna.backward(graph, model, theta, s[:0], cot[:0]).cpu().numpy()
+    assert np.all(z == 0)

@@ -11,8 +11,15 @@ Follows the GNA section of arXiv:2011.12453:
   as (Re log Psi, Im log Psi): the two-head (amplitude, angle) form the conclusion
   proposes for complex wavefunctions.
 
+Nonlinearity f (argument ``act``):
+* "tanh": f = tanh applied elementwise (the configurations built here).
+* "relu_ln": the paper's f, ReLU followed by a layer normalisation over the F features
+  of each node row, r = max(y, 0), f(y) = (r - mean r) / sqrt(mean (r - mean r)^2 + eps).
+  The paper gives neither eps nor an affine part: eps = 1e-6 (LN_EPS), no affine (the
+  next layer's W and b, or the readout, absorb a per-feature scale and shift).
+
 Readings where the paper is silent:
-* f = tanh (no layer normalisation) for the configurations built here.
+* The embedding's nonlinear transform is a dense layer followed by the same f.
 * A is the binary adjacency (couplings J do not enter the network), without
   self-loops; an isolated site has an all-zero row in D^-1/2 A D^-1/2.
 * onehot(+1) = (1, 0) and onehot(-1) = (0, 1); spin +1 is the occupied site
@@ -89,34 +96,62 @@ def onehot(spins: np.ndarray) -> np.ndarray:
     return np.stack([(s > 0), (s < 0)], axis=-1).astype(np.float64)
 
 
-def layers(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, shared: bool = True):
+LN_EPS = 1e-6
+ACTS = ("tanh", "relu_ln")
+
+
+def activation(Y: np.ndarray, act: str = "tanh") -> np.ndarray:
+    """f applied to pre-activations Y (..., F): tanh, or ReLU then layer norm over the last axis."""
+    if act == "tanh":
+        return np.tanh(Y)
+    if act != "relu_ln":
+        raise ValueError(act)
+    r = np.maximum(Y, 0.0)
+    c = r - r.mean(axis=-1, keepdims=True)
+    return c / np.sqrt((c * c).mean(axis=-1, keepdims=True) + LN_EPS)
+
+
+def layers(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, shared: bool = True, act: str = "tanh"):
     """All node-embedding layers [H^0, ..., H^L], each (B, n, F), for a batch of states."""
     p = unpack(theta, F, L, shared)
     x = onehot(np.atleast_2d(spins))
-    H = np.tanh(x @ p["W_e"] + p["b_e"])
+    H = activation(x @ p["W_e"] + p["b_e"], act)
     out = [H]
     for l in range(L):
         msg = np.einsum("vu,buf->bvf", Ahat, H)
-        H = np.tanh(np.concatenate([msg, H], axis=-1) @ p["W"][l] + p["b"][l])
+        H = activation(np.concatenate([msg, H], axis=-1) @ p["W"][l] + p["b"][l], act)
         out.append(H)
     return out
 
 
-def logpsi(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, shared: bool = True) -> np.ndarray:
+def logpsi(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, shared: bool = True,
+           act: str = "tanh") -> np.ndarray:
     """(B, 2) float64: columns (Re log Psi, Im log Psi) for each state of the batch."""
     p = unpack(theta, F, L, shared)
     x = onehot(np.atleast_2d(spins))
-    H = layers(theta, F, L, Ahat, spins, shared)[-1]
+    H = layers(theta, F, L, Ahat, spins, shared, act)[-1]
     z = np.concatenate([H, x], axis=-1).sum(axis=1)  # (B, F+2): sum-pool over sites
     return z @ p["w_r"] + p["b_r"]
 
 
-def logpsi_complex(theta, F, L, Ahat, spins, shared=True) -> np.ndarray:
-    lp = logpsi(theta, F, L, Ahat, spins, shared)
+def logpsi_complex(theta, F, L, Ahat, spins, shared=True, act="tanh") -> np.ndarray:
+    lp = logpsi(theta, F, L, Ahat, spins, shared, act)
     return lp[:, 0] + 1j * lp[:, 1]
 
 
-def logpsi_loops(theta, F: int, L: int, n: int, edges: np.ndarray, spins_1d, shared: bool = True) -> np.ndarray:
+def _f_loops(row, act):
+    """f of one node row (a list of F floats), written with scalar loops."""
+    if act == "tanh":
+        return [float(np.tanh(y)) for y in row]
+    r = [y if y > 0.0 else 0.0 for y in row]
+    mu = sum(r) / len(r)
+    var = sum((x - mu) ** 2 for x in r) / len(r)
+    inv = 1.0 / np.sqrt(var + LN_EPS)
+    return [(x - mu) * inv for x in r]
+
+
+def logpsi_loops(theta, F: int, L: int, n: int, edges: np.ndarray, spins_1d, shared: bool = True,
+                 act: str = "tanh") -> np.ndarray:
     """Same function for ONE state, written with per-site loops over the edge list.
 
     An independent formulation (no dense adjacency matrix, no batched matmul) used to
@@ -132,7 +167,7 @@ def logpsi_loops(theta, F: int, L: int, n: int, edges: np.ndarray, spins_1d, sha
     H = []
     for v in range(n):
         row = p["W_e"][0] if s[v] > 0 else p["W_e"][1]
-        H.append([np.tanh(row[f] + p["b_e"][f]) for f in range(F)])
+        H.append(_f_loops([row[f] + p["b_e"][f] for f in range(F)], act))
     for l in range(L):
         W, b = p["W"][l], p["b"][l]
         newH = []
@@ -147,8 +182,8 @@ def logpsi_loops(theta, F: int, L: int, n: int, edges: np.ndarray, spins_1d, sha
                 acc = b[g]
                 for f in range(F):
                     acc += msg[f] * W[f, g] + H[v][f] * W[F + f, g]
-                row.append(np.tanh(acc))
-            newH.append(row)
+                row.append(acc)
+            newH.append(_f_loops(row, act))
         H = newH
     out = np.array(p["b_r"], dtype=np.float64)
     for v in range(n):

@@ -61,18 +61,33 @@ def cotangents(p: np.ndarray, E: np.ndarray, Ebar: complex) -> np.ndarray:
     return np.stack([2.0 * p * d.real, 2.0 * p * d.imag], axis=1)
 
 
+def _act_vjp(G, H, Y, act):
+    """Cotangent of the pre-activation Y of f, given the cotangent G of H = f(Y).
+
+    tanh: G (1 - H^2).  ReLU then layer norm (r = max(Y, 0), H = (r - mean r)/sigma,
+    sigma = sqrt(var r + eps)): dr = (G - mean G - H mean(G H)) / sigma over each row,
+    then dY = dr where Y > 0 and 0 elsewhere."""
+    if act == "tanh":
+        return G * (1.0 - H * H)
+    r = np.maximum(Y, 0.0)
+    c = r - r.mean(axis=-1, keepdims=True)
+    sigma = np.sqrt((c * c).mean(axis=-1, keepdims=True) + gcn.LN_EPS)
+    dr = (G - G.mean(axis=-1, keepdims=True) - H * (G * H).mean(axis=-1, keepdims=True)) / sigma
+    return np.where(Y > 0.0, dr, 0.0)
+
+
 def backward(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, cot: np.ndarray,
-             shared: bool = True) -> np.ndarray:
+             shared: bool = True, act: str = "tanh") -> np.ndarray:
     """sum_x [cot_x0 d Re log Psi_x/d theta + cot_x1 d Im log Psi_x/d theta] (flat, float64).
 
     Reverse-mode derivative of gcn.logpsi, derived by hand from the chain rule:
-    readout -> L GCN layers (tanh' = 1 - tanh^2; the message term transposes
+    readout -> L GCN layers (f' of _act_vjp; the message term transposes
     D^-1/2 A D^-1/2, which is symmetric) -> embedding.
     """
     p = gcn.unpack(theta, F, L, shared)
     s = np.atleast_2d(spins)
     cot = np.atleast_2d(np.asarray(cot, dtype=np.float64))
-    Hs = gcn.layers(theta, F, L, Ahat, s, shared)
+    Hs = gcn.layers(theta, F, L, Ahat, s, shared, act)
     x = gcn.onehot(s)
     g = {"W_e": np.zeros((2, F)), "b_e": np.zeros(F), "w_r": np.zeros((F + 2, 2)), "b_r": np.zeros(2)}
     gW = [np.zeros((2 * F, F)) for _ in range(L)]
@@ -85,12 +100,12 @@ def backward(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, cot: np
     for l in range(L, 0, -1):
         Hp, Hl = Hs[l - 1], Hs[l]
         X = np.concatenate([np.einsum("vu,buf->bvf", Ahat, Hp), Hp], axis=-1)  # (B, n, 2F)
-        dY = G * (1.0 - Hl * Hl)
+        dY = _act_vjp(G, Hl, X @ p["W"][l - 1] + p["b"][l - 1], act)
         gW[l - 1] += np.einsum("bvk,bvg->kg", X, dY)
         gb[l - 1] += dY.sum(axis=(0, 1))
         dX = dY @ p["W"][l - 1].T  # (B, n, 2F)
         G = np.einsum("uv,buf->bvf", Ahat, dX[..., :F]) + dX[..., F:]
-    dY0 = G * (1.0 - Hs[0] * Hs[0])
+    dY0 = _act_vjp(G, Hs[0], x @ p["W_e"] + p["b_e"], act)
     g["W_e"] += np.einsum("bvc,bvf->cf", x, dY0)
     g["b_e"] += dY0.sum(axis=(0, 1))
     parts = [g["W_e"].ravel(), g["b_e"]]
@@ -103,20 +118,22 @@ def backward(theta, F: int, L: int, Ahat: np.ndarray, spins: np.ndarray, cot: np
     return np.concatenate(parts)
 
 
-def isgo_gradient(theta, F, L, Ahat, edges, J, spins, logpsi0, counts=None, shared=True):
-    """Full ISGO step quantities: (gradient, Ebar, variance, ESS, E_loc, p)."""
+def isgo_gradient(theta, F, L, Ahat, edges, J, spins, logpsi0, counts=None, shared=True, xxz=None,
+                  act="tanh"):
+    """Full ISGO step quantities: (gradient, Ebar, variance, ESS, E_loc, p).  Heisenberg
+    bonds J, or XXZ bonds xxz = (Jz, Jxy, hz, c) (hard-core bosons)."""
     from . import heisenberg
 
     def lp_fn(s):
-        return gcn.logpsi_complex(theta, F, L, Ahat, s, shared)
+        return gcn.logpsi_complex(theta, F, L, Ahat, s, shared, act)
 
     s = np.atleast_2d(spins)
     lp = lp_fn(s)
-    E = heisenberg.local_energy(lp_fn, edges, J, s)
+    E = heisenberg.local_energy(lp_fn, edges, J, s, xxz)
     p = weights(lp, logpsi0, counts)
     Ebar, var, ess = statistics(p, E, counts)
     cot = cotangents(p, E, Ebar)
-    grad = backward(theta, F, L, Ahat, s, cot, shared)
+    grad = backward(theta, F, L, Ahat, s, cot, shared, act)
     return grad, Ebar, var, ess, E, p
 
 

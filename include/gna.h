@@ -8,8 +8,9 @@
  *     GNA section (two readout units: Re and Im of log Psi, the two-head form of the
  *     conclusion);
  *   - the local energy E_x = sum_x' H_xx' Psi_x'/Psi_x and MCMC sampling of
- *     P ~ |Psi|^2 of the scaling section, here for the Heisenberg model
- *     H = sum_<ij> J_ij S_i . S_j;
+ *     P ~ |Psi|^2 of the scaling section, for the Heisenberg model
+ *     H = sum_<ij> J_ij S_i . S_j and, through per-bond XXZ coefficients, the hard-core
+ *     bosons of the numerical-experiments section;
  *   - the ISGO importance-reweighted gradient of Eq. (isgo).
  *
  * Conventions shared by every call:
@@ -64,8 +65,13 @@ typedef int32_t gna_status;
  * samples (energies, weights, gradients) are float64 in every mode. */
 typedef enum { GNA_PREC_FP64 = 0, GNA_PREC_FP32 = 1, GNA_PREC_BF16 = 2 } gna_prec;
 
-/* Nonlinearity f of Eq. (gcn).  TANH is the only one implemented. */
-typedef enum { GNA_ACT_TANH = 0 } gna_act;
+/* Nonlinearity f of Eq. (gcn), also applied after the embedding's dense layer.
+ * TANH: tanh elementwise.  RELU_LN: the GNA section's f, ReLU followed by a layer
+ * normalisation over the F features of each site's row, (r - mean r)/sqrt(var r + 1e-6)
+ * with r = max(y, 0) and no affine part (the paper gives neither eps nor an affine part).
+ * RELU_LN runs at GNA_PREC_FP64 / GNA_PREC_FP32 (calls with GNA_PREC_BF16 return
+ * GNA_ERR_UNSUPPORTED); its Metropolis sweeps take the one-chain-per-CTA kernel. */
+typedef enum { GNA_ACT_TANH = 0, GNA_ACT_RELU_LN = 1 } gna_act;
 
 /* Local-energy evaluation: FULL re-evaluates log Psi of every exchanged configuration
  * (one full GCN forward per antiparallel bond); INCREMENTAL recomputes only the rows of
@@ -123,6 +129,21 @@ GNA_API const char* gna_status_string(gna_status s);
  * Errors: GNA_ERR_INVALID_ARG (checked before any device call), GNA_ERR_CUDA. */
 GNA_API gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const int32_t* edges,
                             const double* J, int32_t max_layers, gna_graph** out);
+
+/* Same graph for bonds of the XXZ family.  The numerical-experiments section of the paper
+ * studies hard-core bosons, H = -t sum_<ij> (b+_i b_j + h.c.) + V sum_<ij> n_i n_j; with
+ * n = (1 + s)/2 and b+ <-> S+ this is, bond by bond,
+ *     H_e = Jz S^z_i S^z_j + Jxy/2 (S+_i S-_j + S-_i S+_j) + hz (S^z_i + S^z_j) + c,
+ * with (Jz, Jxy, hz, c) = (V, -2t, V/2, V/4).  The local energy of a configuration is then
+ *     E_loc(s) = sum_e [Jz/4 s_i s_j + hz/2 (s_i + s_j) + c]
+ *              + sum_{e: s_i != s_j} Jxy/2 Psi(s^e)/Psi(s).
+ * Heisenberg bonds (gna_graph_create) are (J, J, 0, 0).
+ *   Jz, Jxy, hz, c  host float64 [n_edges] each (finite; all four non-NULL when n_edges > 0)
+ * Everything else, and the errors, as gna_graph_create.  The proposal network's coupling
+ * feature is Jxy. */
+GNA_API gna_status gna_graph_create_xxz(int32_t n_sites, int32_t n_edges, const int32_t* edges,
+                                const double* Jz, const double* Jxy, const double* hz,
+                                const double* c, int32_t max_layers, gna_graph** out);
 GNA_API gna_status gna_graph_destroy(gna_graph* g);
 GNA_API gna_status gna_graph_info(const gna_graph* g, int32_t* n_sites, int32_t* n_edges,
                           int32_t* max_layers);

@@ -23,7 +23,10 @@ struct DevGraph {
   const float* wf = nullptr;      // [2E]   1/sqrt(d_v d_u), float32
   const double* wd = nullptr;     // [2E]   same, float64
   const int* edges = nullptr;     // [E][2]
-  const double* J = nullptr;      // [E]
+  const double* J = nullptr;      // [E]    off-diagonal coupling of bond e (J, or Jxy of XXZ bonds)
+  const double* Jz = nullptr;     // [E]    diagonal S^z S^z coupling
+  const double* hz = nullptr;     // [E]    field on both ends of bond e
+  const double* cb = nullptr;     // [E]    constant of bond e
   // Nested neighbourhoods of each bond, for l = 0..Lmax:
   const int* ball_off = nullptr;  // [E+1]  start of bond e's rows in ball_vert / row_nbr
   const int* ball_size = nullptr; // [E][Lmax+1]
@@ -40,13 +43,20 @@ struct DevGraph {
   const int* bond_ent = nullptr;       // [E]    start of bond e's entries in nbr_pos / nbr_pos16
 };
 
+// Diagonal element of bond e's Hamiltonian for S^z eigenvalues s_i/2, s_j/2 (float64):
+// Jz/4 s_i s_j + hz/2 (s_i + s_j) + c.  Heisenberg bonds have Jz = J and hz = c = 0.
+__device__ inline double bond_diag(const DevGraph& g, int e, int si, int sj) {
+  return __ldg(g.Jz + e) * 0.25 * (double)(si * sj) + __ldg(g.hz + e) * 0.5 * (double)(si + sj) +
+         __ldg(g.cb + e);
+}
+
 }  // namespace gna
 
 struct gna_graph {
   gna::DevGraph d;
   int device = 0;
   std::vector<int> h_row_ptr, h_col, h_edges, h_ball_size, h_ball_off;
-  std::vector<double> h_J;
+  std::vector<double> h_J;  // off-diagonal couplings
   std::vector<int> max_ball;  // [Lmax+1] max over bonds of |ball_l|
   std::vector<int> max_span;  // [Lmax+1] max over bonds of sum of degrees over ball_l rows
   int max_deg = 0;
@@ -59,6 +69,7 @@ namespace gna {
 // ---- dims ------------------------------------------------------------------------
 struct Dims {
   int N, E, F, L, shared, P;
+  int act;                         // gna_act: GNA_ACT_TANH or GNA_ACT_RELU_LN
   int oWe, obe, oW, ob, owr, obr;  // parameter offsets (layer l: oW + l*strideW when unshared)
   int strideW;                     // 2F*F + F when unshared, 0 when shared
 };
@@ -70,6 +81,7 @@ inline Dims make_dims(const gna_graph* g, const gna_model_desc* d) {
   m.F = d->F;
   m.L = d->L;
   m.shared = d->shared_weights;
+  m.act = d->act;
   const int F = d->F;
   m.oWe = 0;
   m.obe = 2 * F;

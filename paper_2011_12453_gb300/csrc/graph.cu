@@ -19,7 +19,7 @@ struct HostGraph {
   int n = 0, E = 0, Lmax = 0;
   std::vector<int> row_ptr, col, col_edge, edges;
   std::vector<float> wf;
-  std::vector<double> wd, J;
+  std::vector<double> wd, J, Jz, hz, cb;
   std::vector<int> ball_off, ball_size, ball_vert, row_nbr, nbr_pos, max_ball, max_span;
   std::vector<int> ball_span, row_pack, bond_ent;  // compact forms, see DevGraph
   std::vector<int16_t> nbr_pos16;
@@ -161,15 +161,34 @@ gna_status upload(gna_graph* g, const std::vector<T>& v, const T** dst) {
 
 }  // namespace gna
 
-extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const int32_t* edges,
-                                       const double* J, int32_t max_layers, gna_graph** out) {
-  using namespace gna;
+namespace gna {
+namespace {
+
+// Shared by both creation entries: Jxy is the off-diagonal coupling (J of Heisenberg
+// bonds), Jz / hz / cb the diagonal terms (NULL hz, cb = zero).
+gna_status create_graph(int32_t n_sites, int32_t n_edges, const int32_t* edges, const double* Jz,
+                        const double* Jxy, const double* hz, const double* cb, int32_t max_layers,
+                        gna_graph** out) {
   if (!out) return GNA_ERR_INVALID_ARG;
   *out = nullptr;
-  gna_status st = validate(n_sites, n_edges, edges, J, max_layers, true);
+  gna_status st = validate(n_sites, n_edges, edges, Jxy, max_layers, true);
   if (st != GNA_OK) return st;
+  for (const double* a : {Jz, hz, cb}) {
+    if (a == nullptr) continue;
+    for (int e = 0; e < n_edges; ++e)
+      if (!std::isfinite(a[e])) return GNA_ERR_INVALID_ARG;
+  }
+  if (n_edges > 0 && Jz == nullptr) return GNA_ERR_INVALID_ARG;
   HostGraph h;
-  build(n_sites, n_edges, edges, J, max_layers, &h);
+  build(n_sites, n_edges, edges, Jxy, max_layers, &h);
+  h.Jz.assign(n_edges, 0.0);
+  h.hz.assign(n_edges, 0.0);
+  h.cb.assign(n_edges, 0.0);
+  for (int e = 0; e < n_edges; ++e) {
+    h.Jz[e] = Jz[e];
+    if (hz) h.hz[e] = hz[e];
+    if (cb) h.cb[e] = cb[e];
+  }
   gna_graph* g = new gna_graph();
   cudaGetDevice(&g->device);
   g->d.n = h.n;
@@ -188,6 +207,9 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   UP(h.wd, wd);
   UP(h.edges, edges);
   UP(h.J, J);
+  UP(h.Jz, Jz);
+  UP(h.hz, hz);
+  UP(h.cb, cb);
   UP(h.ball_off, ball_off);
   UP(h.ball_size, ball_size);
   UP(h.ball_vert, ball_vert);
@@ -210,6 +232,22 @@ extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const i
   for (int v = 0; v < h.n; ++v) g->max_deg = std::max(g->max_deg, h.row_ptr[v + 1] - h.row_ptr[v]);
   *out = g;
   return GNA_OK;
+}
+
+}  // namespace
+}  // namespace gna
+
+extern "C" gna_status gna_graph_create(int32_t n_sites, int32_t n_edges, const int32_t* edges,
+                                       const double* J, int32_t max_layers, gna_graph** out) {
+  return gna::create_graph(n_sites, n_edges, edges, J, J, nullptr, nullptr, max_layers, out);
+}
+
+extern "C" gna_status gna_graph_create_xxz(int32_t n_sites, int32_t n_edges, const int32_t* edges,
+                                           const double* Jz, const double* Jxy, const double* hz,
+                                           const double* c, int32_t max_layers, gna_graph** out) {
+  if (n_edges > 0 && (Jz == nullptr || Jxy == nullptr || hz == nullptr || c == nullptr))
+    return GNA_ERR_INVALID_ARG;
+  return gna::create_graph(n_sites, n_edges, edges, Jz, Jxy, hz, c, max_layers, out);
 }
 
 extern "C" gna_status gna_graph_destroy(gna_graph* g) {

@@ -196,26 +196,82 @@ __device__ void load_layer(const Ctx<T>& c, int l) {
   for (int i = threadIdx.x; i < c.F; i += blockDim.x) c.sb[i] = b[i];
 }
 
-// Embedding rows tanh(W_e[c] + b_e) for c = 0 (spin +1) and 1 (spin -1), readout weights.
+// ReLU then layer norm of one row y[0..F) (the GNA section's f): r = max(y, 0),
+// (r - mean r) / sqrt(mean (r - mean r)^2 + eps).  Returns 1/sigma; writes the row when out
+// is not NULL (out may alias y).
+constexpr double kLnEps = 1e-6;
+template <typename T>
+__device__ inline T relu_ln_row(const T* y, int F, T* out) {
+  T mu = 0;
+  for (int f = 0; f < F; ++f) mu += y[f] > (T)0 ? y[f] : (T)0;
+  mu /= (T)F;
+  T var = 0;
+  for (int f = 0; f < F; ++f) {
+    const T d = (y[f] > (T)0 ? y[f] : (T)0) - mu;
+    var += d * d;
+  }
+  const T inv = (T)1 / sqrt(var / (T)F + (T)kLnEps);
+  if (out)
+    for (int f = 0; f < F; ++f) out[f] = ((y[f] > (T)0 ? y[f] : (T)0) - mu) * inv;
+  return inv;
+}
+
+// Reverse of relu_ln_row for one row: y holds the pre-activation on entry and the cotangent
+// of the pre-activation on exit, g the cotangent of the output row h:
+// dy = [y > 0] (g - mean g - h mean(g h)) / sigma.
+template <typename T>
+__device__ inline void ln_vjp_row(T* y, const T* g, const T* h, int F) {
+  const T inv = relu_ln_row(y, F, (T*)nullptr);
+  T mg = 0, mgh = 0;
+  for (int f = 0; f < F; ++f) {
+    mg += g[f];
+    mgh += g[f] * h[f];
+  }
+  mg /= (T)F;
+  mgh /= (T)F;
+  for (int f = 0; f < F; ++f) y[f] = y[f] > (T)0 ? (g[f] - mg - h[f] * mgh) * inv : (T)0;
+}
+
+// Embedding rows f(W_e[c] + b_e) for c = 0 (spin +1) and 1 (spin -1), readout weights.
 template <typename T>
 __device__ void load_fixed(const Ctx<T>& c) {
   const Dims& m = c.a->m;
   const T* th = c.a->theta;
-  for (int i = threadIdx.x; i < 2 * c.F; i += blockDim.x) c.semb[i] = f_tanh(th[m.oWe + i] + th[m.obe + i % c.F]);
+  if (m.act == GNA_ACT_RELU_LN) {
+    // each thread computes its row's statistics itself (F <= 64), then keeps one element
+    for (int i = threadIdx.x; i < 2 * c.F; i += blockDim.x) {
+      const T* we = th + m.oWe + (i / c.F) * c.F;
+      const T* be = th + m.obe;
+      T mu = 0, var = 0;
+      for (int f = 0; f < c.F; ++f) mu += we[f] + be[f] > (T)0 ? we[f] + be[f] : (T)0;
+      mu /= (T)c.F;
+      for (int f = 0; f < c.F; ++f) {
+        const T d = (we[f] + be[f] > (T)0 ? we[f] + be[f] : (T)0) - mu;
+        var += d * d;
+      }
+      const int f0 = i % c.F;
+      const T y0 = we[f0] + be[f0];
+      c.semb[i] = ((y0 > (T)0 ? y0 : (T)0) - mu) * ((T)1 / sqrt(var / (T)c.F + (T)kLnEps));
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * c.F; i += blockDim.x) c.semb[i] = f_tanh(th[m.oWe + i] + th[m.obe + i % c.F]);
+  }
   for (int i = threadIdx.x; i < (c.F + 2) * 2; i += blockDim.x) c.swr[i] = th[m.owr + i];
   if (threadIdx.x < 2) c.sbr[threadIdx.x] = th[m.obr + threadIdx.x];
   if (c.L > 0) load_layer(c, 0);
 }
 
-// out[r][g] = tanh(b[g] + sum_k X[r][k] W[k][g]), r < R.  Four rows per thread.
+// out[r][g] = f(b + X[r] W)[g], r < R, or the pre-activation alone when pre_only.  Four rows
+// per thread.  Called by every thread of the block (ReLU + layer norm synchronises it).
 template <typename T>
-__device__ void rows_gemm_tanh(const Ctx<T>& c, const T* X, int R, T* out) {
+__device__ void rows_gemm_act(const Ctx<T>& c, const T* X, int R, T* out, bool pre_only = false) {
   const int F = c.F, K = 2 * F, ldw = c.ldw;
   const int groups = blockDim.x / F;
   const int g = threadIdx.x % F, rg = threadIdx.x / F;
-  if (rg >= groups) return;
+  const bool ln = c.a->m.act == GNA_ACT_RELU_LN;
+  const bool elementwise = !ln && !pre_only;
   const T bias = c.sb[g];
-  for (int r0 = rg * 4; r0 < R; r0 += groups * 4) {
+  for (int r0 = rg * 4; rg < groups && r0 < R; r0 += groups * 4) {
     const int r1 = min(r0 + 1, R - 1), r2 = min(r0 + 2, R - 1), r3 = min(r0 + 3, R - 1);
     const T* x0 = X + (size_t)r0 * K;
     const T* x1 = X + (size_t)r1 * K;
@@ -230,10 +286,20 @@ __device__ void rows_gemm_tanh(const Ctx<T>& c, const T* X, int R, T* out) {
       a2 += x2[k] * w;
       a3 += x3[k] * w;
     }
-    out[(size_t)r0 * F + g] = f_tanh(a0);
-    if (r0 + 1 < R) out[(size_t)(r0 + 1) * F + g] = f_tanh(a1);
-    if (r0 + 2 < R) out[(size_t)(r0 + 2) * F + g] = f_tanh(a2);
-    if (r0 + 3 < R) out[(size_t)(r0 + 3) * F + g] = f_tanh(a3);
+    if (elementwise) {
+      a0 = f_tanh(a0);
+      a1 = f_tanh(a1);
+      a2 = f_tanh(a2);
+      a3 = f_tanh(a3);
+    }
+    out[(size_t)r0 * F + g] = a0;
+    if (r0 + 1 < R) out[(size_t)(r0 + 1) * F + g] = a1;
+    if (r0 + 2 < R) out[(size_t)(r0 + 2) * F + g] = a2;
+    if (r0 + 3 < R) out[(size_t)(r0 + 3) * F + g] = a3;
+  }
+  if (ln && !pre_only) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) relu_ln_row(out + (size_t)r * F, F, out + (size_t)r * F);
   }
 }
 
@@ -258,7 +324,7 @@ __device__ void forward_all(const Ctx<T>& c, const int8_t* sp, T* Hs, size_t lst
       X[(size_t)v * 2 * F + F + f] = Hp[i];
     }
     __syncthreads();
-    rows_gemm_tanh(c, X, N, Hn);
+    rows_gemm_act(c, X, N, Hn);
     __syncthreads();
   }
   if (!c.a->m.shared && c.L > 1) {
@@ -304,7 +370,7 @@ __device__ void readout(const Ctx<T>& c, const T* HL, const int8_t* sp, double o
 }
 
 // Ordered list of antiparallel bonds (warp 0), and the float64 diagonal energy
-// sum_e J_e/4 s_i s_j.  Returns the count in sint[E + G + ...] slot and diag in sdbl.
+// sum_e of bond e's diagonal element (J_e/4 s_i s_j for Heisenberg bonds).  Returns the count in sint[E + G + ...] slot and diag in sdbl.
 template <typename T>
 __device__ int antiparallel_list(const Ctx<T>& c, const int8_t* sp, int* list, double* diag) {
   const DevGraph& g = c.a->g;
@@ -320,7 +386,7 @@ __device__ int antiparallel_list(const Ctx<T>& c, const int8_t* sp, int* list, d
         const int i = __ldg(g.edges + 2 * e), j = __ldg(g.edges + 2 * e + 1);
         const int si = sp[i], sj = sp[j];
         anti = si != sj;
-        d += __ldg(g.J + e) * 0.25 * (double)(si * sj);
+        d += bond_diag(g, e, si, sj);
       }
       const unsigned mask = __ballot_sync(0xffffffffu, anti);
       if (anti) list[count + __popc(mask & ((1u << lane) - 1u))] = e;
@@ -419,7 +485,7 @@ __device__ void incr_group(const Ctx<T>& c, const IncrLayout<T>& lay, const int8
       lay.X[(size_t)q * 2 * F + F + f] = r < sprev ? nrow[(size_t)r * F + f] : cp[(size_t)v * F + f];
     }
     __syncthreads();
-    rows_gemm_tanh(c, lay.X, R, lay.newl[l]);
+    rows_gemm_act(c, lay.X, R, lay.newl[l]);
     __syncthreads();
   }
   if (!c.a->m.shared && L > 1) load_layer(c, 0);
@@ -972,9 +1038,17 @@ __global__ void __launch_bounds__(kThreadsBwd, 1) k_backward(const SimtArgs<T> a
         for (int k = __ldg(g.row_ptr + v); k < k1; ++k) acc += edge_w<T>(g, k) * Hp[(size_t)__ldg(g.col + k) * F + f];
         X[(size_t)v * 2 * F + f] = acc;
         X[(size_t)v * 2 * F + F + f] = Hp[i];
-        dY[i] = Gb[i] * ((T)1 - Hl[i] * Hl[i]);
+        if (m.act != GNA_ACT_RELU_LN) dY[i] = Gb[i] * ((T)1 - Hl[i] * Hl[i]);
       }
       __syncthreads();
+      if (m.act == GNA_ACT_RELU_LN) {
+        // Y = X W + b again, then per row dY = [Y > 0] (G - mean G - H mean(G H)) / sigma
+        rows_gemm_act(c, X, N, dY, true);
+        __syncthreads();
+        for (int v = threadIdx.x; v < N; v += blockDim.x)
+          ln_vjp_row(dY + (size_t)v * F, Gb + (size_t)v * F, Hl + (size_t)v * F, F);
+        __syncthreads();
+      }
       // dW[k][g] += sum_v X[v][k] dY[v][g] (4 k per thread, two v streams);
       // db[g] += sum_v dY[v][g]
       const size_t oW = m.oW + (size_t)(l - 1) * m.strideW;
@@ -1049,15 +1123,28 @@ __global__ void __launch_bounds__(kThreadsBwd, 1) k_backward(const SimtArgs<T> a
     if (!m.shared && L > 1) {
       load_layer(c, 0);
     }
-    // embedding: dY0 = G (1 - H0^2); dW_e[c][f] += sum_{v: c_v = c} dY0; db_e[f] += sum_v dY0
+    // embedding: dY0 = G f'(Y0); dW_e[c][f] += sum_{v: c_v = c} dY0; db_e[f] += sum_v dY0
+    if (m.act == GNA_ACT_RELU_LN) {
+      for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int row = c.sspin[v] > 0 ? 0 : 1;
+        T* y = dY + (size_t)v * F;
+        for (int f = 0; f < F; ++f) y[f] = a.theta[m.oWe + row * F + f] + a.theta[m.obe + f];
+        ln_vjp_row(y, Gb + (size_t)v * F, cache + (size_t)v * F, F);
+      }
+      __syncthreads();
+    }
     for (int i = threadIdx.x; i < 3 * F; i += blockDim.x) {
       const int f = i % F, which = i / F;  // 0: W_e row up, 1: W_e row down, 2: b_e
       T acc = 0;
       for (int v = 0; v < N; ++v) {
         const bool up = c.sspin[v] > 0;
         if (which == 2 || (which == 0) == up) {
-          const T h = cache[(size_t)v * F + f];
-          acc += Gb[(size_t)v * F + f] * ((T)1 - h * h);
+          if (m.act == GNA_ACT_RELU_LN) {
+            acc += dY[(size_t)v * F + f];
+          } else {
+            const T h = cache[(size_t)v * F + f];
+            acc += Gb[(size_t)v * F + f] * ((T)1 - h * h);
+          }
         }
       }
       part[(which < 2 ? m.oWe + which * F : m.obe) + f] += (double)acc;

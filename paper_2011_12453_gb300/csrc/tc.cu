@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
           const int i = __ldg(a.g.edges + 2 * e), j = __ldg(a.g.edges + 2 * e + 1);
           const int si = c.spin[i], sj = c.spin[j];
           anti = si != sj;
-          d += __ldg(a.g.J + e) * 0.25 * (double)(si * sj);
+          d += bond_diag(a.g, e, si, sj);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, anti);
         if (anti) c.list[count + __popc(mask & ((1u << lane) - 1u))] = e;

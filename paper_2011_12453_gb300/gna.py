@@ -25,13 +25,13 @@ GNA_ERR_UNSUPPORTED = -6
 GNA_WARN_DEGENERATE_WEIGHTS = 1
 
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
-ACT_TANH = 0
+ACT_TANH, ACT_RELU_LN = 0, 1
 ELOC_FULL, ELOC_INCREMENTAL = 0, 1
 OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIGHTS, OP_ISGO_GRAD, \
     OP_METROPOLIS_LEARNED = range(8)
 
 EXPORTED = [
-    "gna_version", "gna_status_string", "gna_graph_create", "gna_graph_destroy", "gna_graph_info",
+    "gna_version", "gna_status_string", "gna_graph_create", "gna_graph_create_xxz", "gna_graph_destroy", "gna_graph_info",
     "gna_ball_sizes_host", "gna_model_desc_init", "gna_num_params", "gna_workspace_size", "gna_forward",
     "gna_local_energy", "gna_metropolis_sweep", "gna_backward", "gna_backward_static", "gna_isgo_weights_workspace",
     "gna_isgo_weights", "isgo_grad",
@@ -76,6 +76,7 @@ def lib():
             "gna_version": (i32, []),
             "gna_status_string": (ctypes.c_char_p, [i32]),
             "gna_graph_create": (i32, [i32, i32, vp, vp, i32, ctypes.POINTER(vp)]),
+            "gna_graph_create_xxz": (i32, [i32, i32, vp, vp, vp, vp, vp, i32, ctypes.POINTER(vp)]),
             "gna_graph_destroy": (i32, [vp]),
             "gna_graph_info": (i32, [vp, vp, vp, vp]),
             "gna_ball_sizes_host": (i32, [i32, i32, vp, i32, vp]),
@@ -147,16 +148,26 @@ def ball_sizes_host(n_sites: int, edges: np.ndarray, n_layers: int) -> np.ndarra
 
 
 class Graph:
-    """Device-resident graph handle (gna_graph_create)."""
+    """Device-resident graph handle: Heisenberg bonds J (gna_graph_create), or XXZ bonds
+    xxz = (Jz, Jxy, hz, c) (gna_graph_create_xxz; J is then ignored)."""
 
-    def __init__(self, n_sites: int, edges: np.ndarray, J: np.ndarray, max_layers: int):
+    def __init__(self, n_sites: int, edges: np.ndarray, J: np.ndarray, max_layers: int, xxz=None):
         e = np.ascontiguousarray(edges, dtype=np.int32)
-        j = np.ascontiguousarray(J, dtype=np.float64)
         h = vp()
         self._h = None
-        _check(lib().gna_graph_create(n_sites, e.shape[0], e.ctypes.data if e.size else None,
-                                      j.ctypes.data if j.size else None, max_layers, ctypes.byref(h)),
-               "gna_graph_create")
+        if xxz is None:
+            j = np.ascontiguousarray(J, dtype=np.float64)
+            _check(lib().gna_graph_create(n_sites, e.shape[0], e.ctypes.data if e.size else None,
+                                          j.ctypes.data if j.size else None, max_layers, ctypes.byref(h)),
+                   "gna_graph_create")
+        else:
+            a = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (e.shape[0],)))
+                 for x in xxz]
+            j = a[1]
+            _check(lib().gna_graph_create_xxz(n_sites, e.shape[0], e.ctypes.data if e.size else None,
+                                              *[x.ctypes.data if x.size else None for x in a],
+                                              max_layers, ctypes.byref(h)),
+                   "gna_graph_create_xxz")
         self._h = h
         self.n_sites = n_sites
         self.n_edges = int(e.shape[0])
@@ -182,11 +193,11 @@ class Graph:
 
 
 class Model:
-    def __init__(self, F: int, L: int, prec: int = PREC_FP64, shared: bool = True):
+    def __init__(self, F: int, L: int, prec: int = PREC_FP64, shared: bool = True, act: int = ACT_TANH):
         self.desc = ModelDesc()
-        _check(lib().gna_model_desc_init(ctypes.byref(self.desc), F, L, ACT_TANH, prec, int(shared)),
+        _check(lib().gna_model_desc_init(ctypes.byref(self.desc), F, L, act, prec, int(shared)),
                "gna_model_desc_init")
-        self.F, self.L, self.prec, self.shared = F, L, prec, bool(shared)
+        self.F, self.L, self.prec, self.shared, self.act = F, L, prec, bool(shared), act
 
     @property
     def num_params(self) -> int:

@@ -43,11 +43,18 @@ def test_num_params_matches_layout(F, L, shared):
     assert m.num_params == W.num_params(F, L, shared)
 
 
-@pytest.mark.parametrize("args", [(0, 2, 0, 0, 1), (65, 2, 0, 0, 1), (16, 9, 0, 0, 1), (16, 2, 1, 0, 1),
+@pytest.mark.parametrize("args", [(0, 2, 0, 0, 1), (65, 2, 0, 0, 1), (16, 9, 0, 0, 1), (16, 2, 2, 0, 1),
                                   (16, 2, 0, 3, 1), (16, 2, 0, 0, 2), (24, 2, 0, 2, 1)])
 def test_model_desc_rejects(args):
     d = gna.ModelDesc()
     assert gna.lib().gna_model_desc_init(ctypes.byref(d), *args) == gna.GNA_ERR_INVALID_ARG
+
+
+def test_model_desc_accepts_relu_ln():
+    d = gna.ModelDesc()
+    for prec in (0, 1, 2):
+        assert gna.lib().gna_model_desc_init(ctypes.byref(d), 16, 3, gna.ACT_RELU_LN, prec, 1) == gna.GNA_OK
+        assert d.act == gna.ACT_RELU_LN
 
 
 def _bfs_balls(n, edges, L):
@@ -113,3 +120,17 @@ def test_isgo_workspace_query():
     n = gna.sz(0)
     assert gna.lib().gna_isgo_weights_workspace(1000, ctypes.byref(n)) == 0 and n.value > 0
     assert gna.lib().gna_isgo_weights_workspace(0, ctypes.byref(n)) == gna.GNA_ERR_INVALID_ARG
+
+
+def test_xxz_graph_validation():
+    e = np.array([[0, 1], [1, 2]], dtype=np.int32)
+    ok = np.ones(2)
+    bad = np.array([1.0, np.inf])
+    h = gna.vp()
+    lib = gna.lib()
+    # any missing coefficient array, or a non-finite one, is rejected on the host
+    for arrs in [(None, ok, ok, ok), (ok, None, ok, ok), (ok, ok, None, ok), (ok, ok, ok, None),
+                 (bad, ok, ok, ok), (ok, bad, ok, ok), (ok, ok, bad, ok), (ok, ok, ok, bad)]:
+        ptrs = [a.ctypes.data if a is not None else None for a in arrs]
+        assert lib.gna_graph_create_xxz(3, 2, e.ctypes.data, *ptrs, 1, ctypes.byref(h)) == gna.GNA_ERR_INVALID_ARG
+        assert not h.value

@@ -41,7 +41,7 @@ static bool desc_ok(const gna_model_desc* d) {
   if (!d) return false;
   if (d->F < 1 || d->F > kMaxF) return false;
   if (d->L < 0 || d->L > kMaxL) return false;
-  if (d->act != GNA_ACT_TANH) return false;
+  if (d->act != GNA_ACT_TANH && d->act != GNA_ACT_RELU_LN) return false;
   if (d->prec < GNA_PREC_FP64 || d->prec > GNA_PREC_BF16) return false;
   if (d->shared_weights != 0 && d->shared_weights != 1) return false;
   if (d->prec == GNA_PREC_BF16 && d->F % 16 != 0) return false;
@@ -50,6 +50,8 @@ static bool desc_ok(const gna_model_desc* d) {
 
 static gna_status check_gd(const gna_graph* g, const gna_model_desc* d) {
   if (!g || !desc_ok(d)) return GNA_ERR_INVALID_ARG;
+  // ReLU + layer norm runs on the float64 / float32 SIMT kernels only
+  if (d->act == GNA_ACT_RELU_LN && d->prec == GNA_PREC_BF16) return GNA_ERR_UNSUPPORTED;
   if (d->L > g->d.Lmax) return GNA_ERR_INVALID_ARG;
   int dev = 0;
   GNA_CUDA_TRY(cudaGetDevice(&dev));
@@ -126,14 +128,19 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
         gna_status st = tcm_workspace(g, m, B, bytes);
         if (st != GNA_ERR_UNSUPPORTED) return st;
       }
-      gna_status st = metro_workspace(g, m, sp, B, 0, bytes);
-      if (st != GNA_ERR_UNSUPPORTED) return st;
+      // the warp sampler propagates tanh differences; ReLU + layer norm takes one chain per CTA
+      if (d->act == GNA_ACT_TANH) {
+        gna_status st = metro_workspace(g, m, sp, B, 0, bytes);
+        if (st != GNA_ERR_UNSUPPORTED) return st;
+      }
       return simt_workspace(g, m, sp, 3, B, bytes);
     }
     case GNA_OP_METROPOLIS_LEARNED: {
       if (g->max_deg > 16) return GNA_ERR_UNSUPPORTED;
-      gna_status st = metro_workspace(g, m, sp, B, 1, bytes);
-      if (st != GNA_ERR_UNSUPPORTED) return st;
+      if (d->act == GNA_ACT_TANH) {
+        gna_status st = metro_workspace(g, m, sp, B, 1, bytes);
+        if (st != GNA_ERR_UNSUPPORTED) return st;
+      }
       return simt_workspace(g, m, sp, 5, B, bytes);
     }
     case GNA_OP_BACKWARD:
@@ -278,7 +285,8 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
                samples_out, logpsi_out, n_accepted, trace};
     return tcm_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
   }
-  if (metro_workspace(g, sc.m, simt_prec(d), C, proposal_params != nullptr, &need) == GNA_OK) {
+  if (d->act == GNA_ACT_TANH &&
+      metro_workspace(g, sc.m, simt_prec(d), C, proposal_params != nullptr, &need) == GNA_OK) {
     MetroCall mc{g, sc.m, theta, chain_spins, C, n_sweeps, record_every, seed, step0,
                  samples_out, logpsi_out, n_accepted, trace, proposal_params, proposal_eps};
     return metro_run(mc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);

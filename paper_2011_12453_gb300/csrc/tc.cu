@@ -602,9 +602,23 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
     const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
     const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = 0; t < dg; ++t) {
-      const int p = np[t];
-      if (p < sprev) fma_chunk(acc, c.wfs[k0 + t], drow + (size_t)p * ldh);
+    // neighbours outside ball_{l-1} have dH = 0: they take weight 0 on a valid row (row 0 of
+    // the bond), so the loop has no branch and keeps two loads in flight; adding the zero
+    // products leaves the sums unchanged
+    int t = 0;
+    for (; t + 2 <= dg; t += 2) {
+      const int p0 = np[t], p1 = np[t + 1];
+      const bool in0 = p0 < sprev, in1 = p1 < sprev;
+      const float w0 = in0 ? c.wfs[k0 + t] : 0.f, w1 = in1 ? c.wfs[k0 + t + 1] : 0.f;
+      const __nv_bfloat16* x0 = drow + (size_t)(in0 ? p0 : 0) * ldh;
+      const __nv_bfloat16* x1 = drow + (size_t)(in1 ? p1 : 0) * ldh;
+      fma_chunk(acc, w0, x0);
+      fma_chunk(acc, w1, x1);
+    }
+    if (t < dg) {
+      const int p0 = np[t];
+      const bool in0 = p0 < sprev;
+      fma_chunk(acc, in0 ? c.wfs[k0 + t] : 0.f, drow + (size_t)(in0 ? p0 : 0) * ldh);
     }
     uint4 w;
     w.x = pack_bf16(acc[0], acc[1]);
@@ -621,6 +635,21 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
 // with e = exp(-2|Y|), H = sgn(Y)(1-e)/(1+e) and 1 - H^2 = 4e/(1+e)^2, so
 // dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t)), t = tanh(dY).
 __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, float* d) {
+  // common case for all 8 units without branches (|dY| < 0.5 and no swing across
+  // saturation); if any unit needs more, all 8 are redone by the full rule below, which gives
+  // the same result as the common case wherever that applies
+  bool slow = false;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float e = fabsf(se[i]);
+    const float sg = se[i] < 0.f ? -1.f : 1.f;
+    const float tt = tanh_fast(dy[i]);
+    const float ope = 1.f + e;
+    const float den = ope * (ope + sg * (1.f - e) * tt);
+    d[i] = __fdividef(4.f * e * tt, den);
+    slow |= !(fabsf(dy[i]) < 0.5f) | !(den > 1e-3f);
+  }
+  if (!slow) return;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float e = fabsf(se[i]);
@@ -1111,14 +1140,28 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
           const float yv[8] = {y[h2][0].x, y[h2][0].y, y[h2][0].z, y[h2][0].w,
                                y[h2][1].x, y[h2][1].y, y[h2][1].z, y[h2][1].w};
           float d[8];
+          // common case without branches, the full rule only when a unit needs it (as delta_tanh8)
+          bool slow = false;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float e = __expf(-2.f * fabsf(yv[i]));
             const float sg = yv[i] < 0.f ? -1.f : 1.f;
-            const float tt = fabsf(dv[i]) < 0.5f ? tanh_fast(dv[i]) : tanhf(dv[i]);
+            const float tt = tanh_fast(dv[i]);
             const float ope = 1.f + e;
             const float den = ope * (ope + sg * (1.f - e) * tt);
-            d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(yv[i] + dv[i]) - tanhf(yv[i]);
+            d[i] = __fdividef(4.f * e * tt, den);
+            slow |= !(fabsf(dv[i]) < 0.5f) | !(den > 1e-3f);
+          }
+          if (slow) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float e = __expf(-2.f * fabsf(yv[i]));
+              const float sg = yv[i] < 0.f ? -1.f : 1.f;
+              const float tt = fabsf(dv[i]) < 0.5f ? tanh_fast(dv[i]) : tanhf(dv[i]);
+              const float ope = 1.f + e;
+              const float den = ope * (ope + sg * (1.f - e) * tt);
+              d[i] = den > 1e-3f ? __fdividef(4.f * e * tt, den) : tanhf(yv[i] + dv[i]) - tanhf(yv[i]);
+            }
           }
           if (l < L) {
             uint4 w;

@@ -573,9 +573,15 @@ __device__ void tc_readout(const TcCtx& c, double out[2]) {
 }
 
 // Slot of group row q at layer l (offsets offl[0..nb]).
+// Branch-free binary search for the largest k < nb with offl[k] <= q (offl strictly
+// increasing, offl[0] = 0 <= q; nb <= 16).
 __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
   int k = 0;
-  while (k + 1 < nb && offl[k + 1] <= q) ++k;
+#pragma unroll
+  for (int step = 8; step >= 1; step >>= 1) {
+    const int j = k + step;
+    if (j < nb && offl[j] <= q) k = j;
+  }
   return k;
 }
 
@@ -926,17 +932,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
       unit_sync(u);
       if (!tc_group(c, u, nb)) break;
+      // each bond's term Jxy/2 exp(Delta) by its own lane (in place of its Delta), then
+      // thread 0 adds them in bond order
+      if (u.tid < nb) {
+        const int k = u.tid, e = u.slot_e[k];
+        const float dre = (float)u.res[2 * k], dim = (float)u.res[2 * k + 1];
+        const float amp = expf(dre);
+        float sn, cs;
+        sincosf(dim, &sn, &cs);
+        const double J = __ldg(a.g.J + e);
+        u.res[2 * k] = 0.5 * J * (double)(amp * cs);
+        u.res[2 * k + 1] = 0.5 * J * (double)(amp * sn);
+        if (a.dlogpsi) a.dlogpsi[b * c.E + e] = dre;
+      }
+      __syncwarp();
       if (u.tid == 0) {
         for (int k = 0; k < nb; ++k) {
-          const int e = u.slot_e[k];
-          const float dre = (float)u.res[2 * k], dim = (float)u.res[2 * k + 1];
-          const float amp = expf(dre);
-          float sn, cs;
-          sincosf(dim, &sn, &cs);
-          const double J = __ldg(a.g.J + e);
-          er += 0.5 * J * (double)(amp * cs);
-          ei += 0.5 * J * (double)(amp * sn);
-          if (a.dlogpsi) a.dlogpsi[b * c.E + e] = dre;
+          er += u.res[2 * k];
+          ei += u.res[2 * k + 1];
         }
       }
       unit_sync(u);

@@ -213,11 +213,14 @@ struct TcArgs {
   int region_in_smem;
 };
 
-// F <= 32: two 256-thread units; wider features: four 128-thread units (more independent
-// rounds in flight per SM).  One 128-row tile per unit and pass: the shared memory goes to
-// larger bond groups instead (measured at Kagome 108, F = 32: two tiles and 4 bonds per
-// group 43.3 ms, one tile and 6 bonds 41.9 ms).
+// Local energy and forward: F <= 32 two 256-thread units, wider features four 128-thread
+// units (more independent rounds in flight per SM).  The sampler takes four units from
+// F = 32 on (Kagome 108, F = 32, 16384 chains: two units 31.3 ms per sweep, four 26.9 ms;
+// the local energy with four units: 33.6 ms instead of 30.8).  One 128-row tile per unit
+// and pass: the shared memory goes to larger bond groups instead (measured at Kagome 108,
+// F = 32: two tiles and 4 bonds per group 43.3 ms, one tile and 6 bonds 41.9 ms).
 __host__ inline int tc_units(int F) { return F <= 32 ? 2 : 4; }
+__host__ inline int tcm_units(int F) { return F <= 16 ? 2 : 4; }
 __host__ inline int tc_tiles_per_unit(int) { return 1; }
 
 // Passes of rows_per_pass rows that a group of G bonds needs over layers 1..L, per bond
@@ -2057,7 +2060,7 @@ static void tcm_layout(const Dims& m, const int* maxball, int maxspan, int G, in
     return (uint32_t)r;
   };
   t->T = tc_tiles_per_unit(F);
-  t->units = tc_units(F);
+  t->units = tcm_units(F);
   const int U = t->units, unit_threads = kTcThreads / U;
   t->G = G;
   t->a_unit = (uint32_t)t->T * 128 * 2 * F * 2;
@@ -2107,7 +2110,7 @@ static gna_status tcm_plan(const gna_graph* g, const Dims& m, int64_t C, TcmPlan
   if (di.cc < 100) return GNA_ERR_UNSUPPORTED;
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
   const int maxspan = g->max_span[m.L];
-  const int T = tc_tiles_per_unit(m.F), U = tc_units(m.F);
+  const int T = tc_tiles_per_unit(m.F), U = tcm_units(m.F);
   if (U * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   // pool size: up to 8 chains with their dH rows in shared memory; when fewer than 4 fit
   // there, pools of 8 with the dH rows in the workspace (deep layers then take several

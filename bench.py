@@ -298,10 +298,10 @@ def run_reference(a):
 PROFILED_TRAFFIC = {
     # ncu --set full, 2048 configurations, one launch: 484,096 B read + 0 B written
     ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 484096 / 2048,
-                                          "sha256": "229e780c18cdc2ae1203a5b140e5fceb683c3eb5f019cf922f06df46ff8a19ca"},
-    # ncu --set full, 2048 chains, one sweep: 475,938,560 B read + 1,422,164,000 B written
-    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (475938560 + 1422164000) / 2048,
-                                                "sha256": "229e780c18cdc2ae1203a5b140e5fceb683c3eb5f019cf922f06df46ff8a19ca"},
+                                          "sha256": "5bde9ebb4eaba6903d0c54d2bca797708c6d86fc94c51a44acb54ddaf6cfaaf2"},
+    # ncu --set full, 2048 chains, one sweep: 479,169,024 B read + 1,430,542,000 B written
+    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (479169024 + 1430542000) / 2048,
+                                                "sha256": "5bde9ebb4eaba6903d0c54d2bca797708c6d86fc94c51a44acb54ddaf6cfaaf2"},
 }
 
 

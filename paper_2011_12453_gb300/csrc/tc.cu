@@ -928,10 +928,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       for (int e = threadIdx.x; e < c.E; e += blockDim.x) a.dlogpsi[b * c.E + e] = 0.f;
     __syncthreads();
     const int na = s_count;
-    // unit h takes the bond groups h, h + U, ...
+    // unit h takes the h-th of U equal shares of the antiparallel bonds, in groups of up to
+    // G bonds (equal shares keep the units' work balanced up to one bond)
     double er = 0.0, ei = 0.0;
-    for (int t0 = h * c.G; t0 < na; t0 += U * c.G) {
-      const int nb = min(c.G, na - t0);
+    const int b_lo = (int)((int64_t)na * h / U), b_hi = (int)((int64_t)na * (h + 1) / U);
+    for (int t0 = b_lo; t0 < b_hi; t0 += c.G) {
+      const int nb = min(c.G, b_hi - t0);
       if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
       unit_sync(u);
       if (!tc_group(c, u, nb)) break;

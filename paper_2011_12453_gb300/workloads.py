@@ -128,6 +128,17 @@ def erdos_renyi(n: int, p: float, seed: int, J_range: tuple[float, float] | None
     raise RuntimeError("no connected sample found")
 
 
+def random_graph_set(count: int = 32, seed: int = 1000, n_range: tuple[int, int] = (32, 96),
+                     mean_degree: float = 4.0) -> list[Graph]:
+    """`count` Erdos-Renyi graphs: sizes uniform in n_range (inclusive, drawn from `seed`),
+    edge probability mean_degree/(n - 1), couplings J uniform in [0.5, 1.5]; graph g is
+    erdos_renyi with seed `seed` + 1000 * (g + 1) (resampled until connected)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_range[0], n_range[1] + 1, size=count)
+    return [erdos_renyi(int(n), mean_degree / (int(n) - 1), seed + 1000 * (g + 1), J_range=(0.5, 1.5))
+            for g, n in enumerate(sizes)]
+
+
 def two_site() -> Graph:
     """Two sites joined by one bond (the singlet/triplet test system)."""
     return Graph(2, np.array([[0, 1]], dtype=np.int32), np.ones(1), "two_site")

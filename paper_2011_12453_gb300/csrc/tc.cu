@@ -1258,6 +1258,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_fail;
   __shared__ int s_more[kTcMaxUnits];
+  __shared__ uint32_t s_dyoff[kMaxL + 1];  // a.dy_off, indexed by a runtime layer
   const TcArgs& b = a.base;
   TcCtx c;
   c.a = &b;
@@ -1290,6 +1291,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int h = 0; h < b.lay.units; ++h) mbar_init(bars + h, 1);
+    for (int l = 0; l <= kMaxL; ++l) s_dyoff[l] = (uint32_t)a.dy_off[l];
   }
   if ((threadIdx.x >> 5) == 0) {
     tmem_alloc(slot, kTmemCols);
@@ -1482,27 +1484,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
           }
         }
         unit_sync(u);
-        // 4. accepted moves: Y += dY on the bond's balls, exchange the spins
+        // 4. accepted moves: Y += dY on the bond's balls, exchange the spins.  The items
+        //    (layer, ball row, 4 features) of an accepted bond are spread over the unit's
+        //    threads, two per thread per round with every load issued before the stores,
+        //    so that their L2 latencies overlap (rows and sizes from the staged tables)
         for (int k = 0; k < nb; ++k) {
           if (!S.ok[k]) continue;
           const int s = S.gslot[k], e = u.slot_e[k];
           float* sl = tcm_slot(a, ug, s);
-          const int bo = __ldg(b.g.ball_off + e);
-          for (int l = 1; l <= L; ++l) {
-            const int R = __ldg(b.g.ball_size + (size_t)e * (b.g.Lmax + 1) + l);
-            float* Y = sl + (size_t)(l - 1) * N * F;
-            const float* dY = sl + a.dy_off[l];
-            for (int i = u.tid; i < R * (F / 4); i += u.nthr) {
-              const int r = i / (F / 4), f4 = i - r * (F / 4);
-              const int v = __ldg(b.g.ball_vert + bo + r);
-              float4* y = reinterpret_cast<float4*>(Y + (size_t)v * F) + f4;
-              const float4 d = reinterpret_cast<const float4*>(dY + (size_t)r * F)[f4];
-              float4 t = *y;
-              t.x += d.x;
-              t.y += d.y;
-              t.z += d.z;
-              t.w += d.w;
-              *y = t;
+          const int F4 = F / 4;
+          const int* rows = u.srow + u.soff[L * (G + 1) + k];
+          int total = 0;
+          for (int l = 1; l <= L; ++l) total += (u.soff[l * (G + 1) + k + 1] - u.soff[l * (G + 1) + k]) * F4;
+          for (int i0 = u.tid; i0 < total; i0 += 2 * u.nthr) {
+            int yo[2];  // float offset of the item's Y in the slot, -1 past the end
+            float4 yv[2], dv[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const int i = i0 + j * u.nthr;
+              yo[j] = -1;
+              if (i < total) {
+                int l = 1, base = 0;
+                for (;;) {
+                  const int nl = (u.soff[l * (G + 1) + k + 1] - u.soff[l * (G + 1) + k]) * F4;
+                  if (i - base < nl || l == L) break;
+                  base += nl;
+                  ++l;
+                }
+                const int idx = i - base, r = idx / F4, f4 = idx - r * F4;
+                yo[j] = (l - 1) * N * F + (rows[r] & 0xFFFF) * F + 4 * f4;
+                yv[j] = *reinterpret_cast<const float4*>(sl + yo[j]);
+                dv[j] = *reinterpret_cast<const float4*>(sl + s_dyoff[l] + r * F + 4 * f4);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              if (yo[j] < 0) continue;
+              float4 t = yv[j];
+              t.x += dv[j].x;
+              t.y += dv[j].y;
+              t.z += dv[j].z;
+              t.w += dv[j].w;
+              *reinterpret_cast<float4*>(sl + yo[j]) = t;
             }
           }
           if (u.tid == 0) {

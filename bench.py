@@ -296,12 +296,12 @@ def run_reference(a):
 # dram__bytes_write.sum of one launch / the samples it processed), valid only for the source file
 # that was profiled: keyed by (workload, kernel) with the SHA-256 of that source.
 PROFILED_TRAFFIC = {
-    # ncu --set full, 2048 configurations, one launch: 484,096 B read + 0 B written
-    ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 484096 / 2048,
-                                          "sha256": "5bde9ebb4eaba6903d0c54d2bca797708c6d86fc94c51a44acb54ddaf6cfaaf2"},
-    # ncu --set full, 2048 chains, one sweep: 479,169,024 B read + 1,430,542,000 B written
-    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (479169024 + 1430542000) / 2048,
-                                                "sha256": "5bde9ebb4eaba6903d0c54d2bca797708c6d86fc94c51a44acb54ddaf6cfaaf2"},
+    # ncu --set full, 2048 configurations, one launch: 479,488 B read + 0 B written
+    ("kagome_6x6x3_heisenberg", "k_tc"): {"bytes_per_unit": 479488 / 2048,
+                                          "sha256": "ba7b6fcd9a321f596e152f94783b5f400016bf8b9b757818811f934a98a5fe52"},
+    # ncu --set full, 2048 chains, one sweep: 480,592,384 B read + 1,434,398,000 B written
+    ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (480592384 + 1434398000) / 2048,
+                                                "sha256": "ba7b6fcd9a321f596e152f94783b5f400016bf8b9b757818811f934a98a5fe52"},
 }
 
 

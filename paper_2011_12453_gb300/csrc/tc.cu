@@ -144,6 +144,50 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return y;
 }
 
+// Pairs of float32 in one 64-bit register, for the f32x2 arithmetic of sm_100 and later
+// (one instruction does both halves).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Common case of the tanh difference for two units: e = exp(-2|Y|), s = a value with the
+// sign of Y, t = tanh(dY); returns d = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t)) for
+// both and the two denominators, in f32x2 arithmetic (used by the local energy; in the
+// sampler, whose registers are fuller, the packed form spilled and was slower).
+__device__ __forceinline__ void delta_tanh_pair(float e0, float e1, float s0, float s1, float t0, float t1,
+                                                float& d0, float& d1, float& den0, float& den1) {
+  const uint64_t E = pk2(e0, e1), T = pk2(t0, t1);
+  const uint64_t ope = add2(E, pk2(1.f, 1.f));
+  const uint64_t g = pk2(copysignf(1.f - e0, s0), copysignf(1.f - e1, s1));
+  const uint64_t den = mul2(ope, fma2(g, T, ope));
+  upk2(den, den0, den1);
+  float r0, r1;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(den0));
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r1) : "f"(den1));
+  const uint64_t r4 = mul2(pk2(r0, r1), pk2(4.f, 4.f));
+  upk2(mul2(mul2(E, T), r4), d0, d1);
+}
+
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -649,14 +693,11 @@ __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, fl
   // the same result as the common case wherever that applies
   bool slow = false;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float e = fabsf(se[i]);
-    const float sg = se[i] < 0.f ? -1.f : 1.f;
-    const float tt = tanh_fast(dy[i]);
-    const float ope = 1.f + e;
-    const float den = ope * (ope + sg * (1.f - e) * tt);
-    d[i] = __fdividef(4.f * e * tt, den);
-    slow |= !(fabsf(dy[i]) < 0.5f) | !(den > 1e-3f);
+  for (int i = 0; i < 8; i += 2) {
+    float den0, den1;
+    delta_tanh_pair(fabsf(se[i]), fabsf(se[i + 1]), se[i], se[i + 1], tanh_fast(dy[i]), tanh_fast(dy[i + 1]), d[i],
+                    d[i + 1], den0, den1);
+    slow |= !(fabsf(dy[i]) < 0.5f) | !(den0 > 1e-3f) | !(fabsf(dy[i + 1]) < 0.5f) | !(den1 > 1e-3f);
   }
   if (!slow) return;
 #pragma unroll

@@ -460,6 +460,15 @@ __device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, const Unit& u, i
   return (__nv_bfloat16*)((unsigned char*)u.d16 + c.a->lay.new16_off[l]);
 }
 
+// acc2[0..4) (pairs of float32) += w * bf16 row chunk at p (16 bytes), f32x2 arithmetic
+__device__ __forceinline__ void fma_chunk2(uint64_t* acc2, uint64_t w2, const __nv_bfloat16* p) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  acc2[0] = fma2(pk2(bf16lo(u.x), bf16hi(u.x)), w2, acc2[0]);
+  acc2[1] = fma2(pk2(bf16lo(u.y), bf16hi(u.y)), w2, acc2[1]);
+  acc2[2] = fma2(pk2(bf16lo(u.z), bf16hi(u.z)), w2, acc2[2]);
+  acc2[3] = fma2(pk2(bf16lo(u.w), bf16hi(u.w)), w2, acc2[3]);
+}
+
 // acc[0..8) += w * bf16 row chunk at p (16 bytes)
 __device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat16* p) {
   const uint4 u = *reinterpret_cast<const uint4*>(p);
@@ -654,7 +663,7 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
     const int v = rec & 0xFFFF;
     const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
     const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
-    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t acc2[4] = {0, 0, 0, 0};  // pairs of float32 zeros
     // neighbours outside ball_{l-1} have dH = 0: they take weight 0 on a valid row (row 0 of
     // the bond), so the loop has no branch and keeps two loads in flight; adding the zero
     // products leaves the sums unchanged
@@ -665,14 +674,20 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
       const float w0 = in0 ? c.wfs[k0 + t] : 0.f, w1 = in1 ? c.wfs[k0 + t + 1] : 0.f;
       const __nv_bfloat16* x0 = drow + (size_t)(in0 ? p0 : 0) * ldh;
       const __nv_bfloat16* x1 = drow + (size_t)(in1 ? p1 : 0) * ldh;
-      fma_chunk(acc, w0, x0);
-      fma_chunk(acc, w1, x1);
+      fma_chunk2(acc2, pk2(w0, w0), x0);
+      fma_chunk2(acc2, pk2(w1, w1), x1);
     }
     if (t < dg) {
       const int p0 = np[t];
       const bool in0 = p0 < sprev;
-      fma_chunk(acc, in0 ? c.wfs[k0 + t] : 0.f, drow + (size_t)(in0 ? p0 : 0) * ldh);
+      const float w0 = in0 ? c.wfs[k0 + t] : 0.f;
+      fma_chunk2(acc2, pk2(w0, w0), drow + (size_t)(in0 ? p0 : 0) * ldh);
     }
+    float acc[8];
+    upk2(acc2[0], acc[0], acc[1]);
+    upk2(acc2[1], acc[2], acc[3]);
+    upk2(acc2[2], acc[4], acc[5]);
+    upk2(acc2[3], acc[6], acc[7]);
     uint4 w;
     w.x = pack_bf16(acc[0], acc[1]);
     w.y = pack_bf16(acc[2], acc[3]);

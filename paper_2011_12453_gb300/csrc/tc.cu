@@ -1804,16 +1804,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
     if (!ok) break;
     ++nsamples;
     const float c0 = (float)a.cot[2 * bi], c1 = (float)a.cot[2 * bi + 1];
-    // readout: d w_r[f] += cot z_f with z = sum_v [H^L_v ; onehot_v]; d b_r += cot
+    // readout: d w_r[f] += cot z_f with z = sum_v [H^L_v ; onehot_v]; d b_r += cot.  The
+    // column sums over sites run on the whole block: P interleaved site strides per feature,
+    // their FP32 partials (in the free dX buffer) added in a fixed order
     const float* seL = cacheY(c, L);
-    for (int f = threadIdx.x; f < F + 2; f += blockDim.x) {
+    const int P = min((int)blockDim.x / F, N), fcol = threadIdx.x % F, part = threadIdx.x / F;
+    if (part < P) {
+      float zz = 0.f;
+      for (int v = part; v < N; v += P) {
+        const float se = seL[(size_t)v * ldy + fcol], e = fabsf(se);
+        zz += copysignf(__fdividef(1.f - e, 1.f + e), se);
+      }
+      dx[part * F + fcol] = zz;
+    }
+    __syncthreads();
+    if (threadIdx.x < F + 2) {
+      const int f = threadIdx.x;
       double z = 0.0;
       if (f < F) {
         float zz = 0.f;
-        for (int v = 0; v < N; ++v) {
-          const float se = seL[(size_t)v * ldy + f], e = fabsf(se);
-          zz += copysignf(__fdividef(1.f - e, 1.f + e), se);
-        }
+        for (int q = 0; q < P; ++q) zz += dx[q * F + f];
         z = (double)zz;
       } else {
         int cnt = 0;
@@ -1835,14 +1845,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
     for (int l = L; l >= 1 && ok; --l) {
       const float* se = cacheY(c, l);
       const __nv_bfloat16* hp = cache16(c, l - 1);
-      // db += sum_v dY^l_v
-      for (int f = threadIdx.x; f < F; f += blockDim.x) {
-        float s = 0.f;
-        for (int v = 0; v < N; ++v) {
-          const float e = fabsf(se[(size_t)v * ldy + f]), ope = 1.f + e;
-          s += Gs[(size_t)v * F + f] * __fdividef(4.f * e, ope * ope);
+      // db += sum_v dY^l_v (block-wide column sums as for the readout; dX is free here)
+      if (part < P) {
+        float sum = 0.f;
+        for (int v = part; v < N; v += P) {
+          const float e = fabsf(se[(size_t)v * ldy + fcol]), ope = 1.f + e;
+          sum += Gs[(size_t)v * F + fcol] * __fdividef(4.f * e, ope * ope);
         }
-        sp[sp_b(F) + f] += (double)s;
+        dx[part * F + fcol] = sum;
+      }
+      __syncthreads();
+      if (threadIdx.x < F) {
+        float sum = 0.f;
+        for (int q = 0; q < P; ++q) sum += dx[q * F + threadIdx.x];
+        sp[sp_b(F) + threadIdx.x] += (double)sum;
       }
       for (int c0s = 0; c0s < N && ok; c0s += 128) {
         const int ns = min(128, N - c0s);
@@ -1954,13 +1970,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
     }
     if (!ok) break;
     // embedding: dY^0 = G^0 (1 - emb^2); d W_e[c] += sum_{v: c_v = c} dY^0_v, d b_e += sum_v dY^0_v
+    // (block-wide column sums of the up and the down sites, partials in the free dX buffer)
+    if (part < P) {
+      float su = 0.f, sd = 0.f;
+      for (int v = part; v < N; v += P) {
+        if (c.spin[v] > 0)
+          su += Gs[(size_t)v * F + fcol];
+        else
+          sd += Gs[(size_t)v * F + fcol];
+      }
+      dx[part * F + fcol] = su;
+      dx[(P + part) * F + fcol] = sd;
+    }
+    __syncthreads();
     for (int f = threadIdx.x; f < F; f += blockDim.x) {
       float su = 0.f, sd = 0.f;
-      for (int v = 0; v < N; ++v) {
-        if (c.spin[v] > 0)
-          su += Gs[(size_t)v * F + f];
-        else
-          sd += Gs[(size_t)v * F + f];
+      for (int q = 0; q < P; ++q) {
+        su += dx[q * F + f];
+        sd += dx[(P + q) * F + f];
       }
       const float eu = c.emb[f], ed = c.emb[F + f];
       const double du = (double)(su * (1.f - eu * eu)), dd = (double)(sd * (1.f - ed * ed));

@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default=os.environ.get("GNA_BENCH_PREC", "auto"))
+    p.add_argument("--backward-prec", default="same", choices=["same", "fp32"],
+                   help="arithmetic of the step's backward: that of --prec (default) or FP32, whose ISGO "
+                        "gradient stays accurate at nearly flat wavefunctions")
     p.add_argument("--workload", default="kagome108", choices=sorted(WORKLOADS))
     p.add_argument("--chains", type=int, default=None, help="override the workload's chain count")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -362,6 +365,7 @@ def run_ours(a):
     prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32}[prec_name]
     model = gna.Model(F, L, prec)
     model32 = gna.Model(F, L, gna.PREC_FP32)
+    model_bwd = model32 if a.backward_prec == "fp32" else model
     theta = torch.tensor(W.random_theta(F, L, wl["theta_seed"]), dtype=torch.float32, device=dev)
     chains = torch.tensor(W.random_spins(N, C, wl["spin_seed"] + 1000 * rank), device=dev)
     P = model.num_params
@@ -399,7 +403,7 @@ def run_ours(a):
             mark("local_energy")
             cot, stats = gna.isgo_weights(lp, l0, E)
             mark("isgo_weights")
-            gna.backward(graph, model, theta, s, cot, out=grad)
+            gna.backward(graph, model_bwd, theta, s, cot, out=grad)
             gna.sgd_update(model, theta, grad, lr)
             mark("backward_sgd")
         state["step"] += 1
@@ -525,7 +529,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec_name, "data": "synthetic",
             "config": dict(cfg, samples_per_step=Bn, l2="flushed between timed steps (512 MiB write)",
-                           parallelism=f"replicas{ws}"),
+                           parallelism=f"replicas{ws}",
+                           backward=prec_name if a.backward_prec == "same" else a.backward_prec),
             "isgo_step_ms": float(ph[:, 1:].sum(axis=1).mean()) / K,
             "phases_ms": {n: float(ph[:, i].mean()) for i, n in enumerate(names)},
             "comparator": {"samples": nc,

@@ -328,6 +328,16 @@ extern "C" gna_status gna_backward_static(const gna_graph* g, const gna_model_de
   if (st != GNA_OK) return st;
   if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
   if (!theta || !grad || (B > 0 && (!spins || !cot))) return GNA_ERR_INVALID_ARG;
+  // BF16 models: the tensor-core backward of gna_backward, with its scratch in the fixed array
+  size_t need = 0;
+  if (d->prec == GNA_PREC_BF16 && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
+    void* base = nullptr;
+    size_t bytes = 0;
+    st = static_scratch(&base, &bytes);
+    if (st != GNA_OK) return st;
+    TcbCall tc{g, make_dims(g, d), (const float*)theta, spins, B, cot, grad};
+    return tcb_run_fixed(tc, base, bytes, (cudaStream_t)stream);
+  }
   SimtCall sc{};
   sc.g = g;
   sc.m = make_dims(g, d);

@@ -143,6 +143,8 @@ struct SimtCall {
 gna_status simt_workspace(const gna_graph* g, const Dims& m, int prec, int op, int64_t B, size_t* bytes);
 gna_status simt_run(const SimtCall& sc, int prec, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status simt_backward_static(const SimtCall& sc, int prec, cudaStream_t stream);
+// Device address and size of the library's fixed backward scratch array on the current device.
+gna_status static_scratch(void** base, size_t* bytes);
 size_t dedup_workspace(int64_t B, int N);
 gna_status dedup_run(int N, const int8_t* spins, const double* logpsi, int64_t B, int8_t* us, double* ul, double* uc,
                      int64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t st);

@@ -1411,6 +1411,11 @@ static gna_status backward_static_launch(const SimtCall& sc, cudaStream_t stream
   return GNA_OK;
 }
 
+gna_status static_scratch(void** base, size_t* bytes) {
+  *bytes = kStaticScratchBytes;
+  return static_scratch_address(base);
+}
+
 gna_status simt_backward_static(const SimtCall& sc, int prec, cudaStream_t stream) {
   return prec == GNA_PREC_FP64 ? backward_static_launch<double>(sc, stream) : backward_static_launch<float>(sc, stream);
 }

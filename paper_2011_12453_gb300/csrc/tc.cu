@@ -1666,30 +1666,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
-// Backward VJP on the tensor cores (BF16 models)
+// Backward VJP on the tensor cores (BF16 models), split operands
 // ---------------------------------------------------------------------------------
 // grad = sum_x [cot_re,x d Re log Psi_x + cot_im,x d Im log Psi_x] / d theta (the ISGO
-// cotangents, Eq. isgo).  Per configuration: the tensor-core forward keeps H^0..H^{L-1}
-// (BF16) and copysign(exp(-2|Y^l|), Y^l) (FP32, giving 1 - (H^l)^2 = 4e/(1+e)^2 without
-// cancellation); then, from G^L_v = cot . w_r[:F] (the same for every site), for
-// l = L..1:
+// cotangents, Eq. isgo).  The cotangents sum to zero over the batch, so where the
+// wavefunction is nearly flat the gradient is a small difference of per-sample derivatives
+// that are nearly equal: BF16 rounding of the activations (relative 2^-8 of the full
+// derivatives) would cost most of the result.  Every FP32 operand x of a tensor-core product
+// is therefore carried as two BF16 values, hi = bf16(x) and lo = bf16(x - hi) (about 16
+// significant bits), and the products are accumulated in FP32 in tensor memory; W is a BF16
+// model parameter and needs no split.  Activations are kept in FP32 with an accurate tanh.
+//
+// Per configuration: the forward keeps H^1..H^L (FP32), with H^0 the embedding row of each
+// site's spin; then, from G^L_v = cot . w_r[:F] (the same for every site), for l = L..1:
 //   dY^l = G^l (1 - (H^l)^2)                                   (SIMT, FP32)
-//   dW  += X^T dY^l,  X = [A_hat H^{l-1} ; H^{l-1}]            (MMA: M = 2F padded to 128,
-//                                                               N = F, K = sites in chunks
-//                                                               of 128; the accumulator
-//                                                               stays in TMEM for the whole
-//                                                               launch -- W is shared)
+//   dW  += X^T dY^l,  X = [A_hat H^{l-1} ; H^{l-1}]            (MMA: M = rows of X^T (2F, hi
+//                                                               and lo stacked when 4F <= 128,
+//                                                               else one tile each), N = F,
+//                                                               K = sites in chunks of 128;
+//                                                               the accumulator stays in TMEM
+//                                                               for the whole launch -- W is
+//                                                               shared)
 //   dX   = dY^l W^T                                             (MMA: M = sites, N = 2F, K = F)
 //   G^{l-1}_v = dX_v[F:] + sum_u A_hat_vu dX_u[:F]              (SIMT gather, FP32)
 //   db  += sum_v dY^l_v
 // and the embedding and readout terms in FP64 shared accumulators.  Per-CTA partials of
 // all P parameters (FP64) are summed in a fixed order by a second kernel.
 struct TcbArgs {
-  TcArgs base;         // graph, dims, theta, spins, B; layout of the forward pieces
+  TcArgs base;         // graph, dims, theta, spins, B; layout of the shared pieces
   const double* cot;   // [B][2]
   double* partial;     // [grid][P]
   uint32_t oWb, oXt, odYt, osp;  // smem: W as the B operand of dX; X^T and dY^T tiles; FP64 accumulators
-  uint64_t rG, rdx;    // region: G [N][F] and dX [N][2F] (FP32)
+  int xt_packed;       // 1: X^T hi in rows [0, 2F) and lo in rows [2F, 4F) of one tile (4F <= 128)
+  uint64_t rH, rG, rdx;  // region: H^1..H^L [L][N][F+4], G [N][F] and dX [N][2F] (FP32)
 };
 
 // element (r, k) of a K-column tile in the no-swizzle K-major canonical layout
@@ -1707,11 +1716,132 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint32_t a_addr, uint
              (accumulate || kb > 0) ? 1u : 0u);
 }
 
+// 8 FP32 values as hi = bf16(x) and lo = bf16(x - hi), packed two per 32-bit word.
+__device__ __forceinline__ void split_hi_lo(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
+    h[p] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[p] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// one element as hi and lo BF16
+__device__ __forceinline__ void split1(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// acc[0..8) += w * FP32 row chunk at p (two 16-byte loads)
+__device__ __forceinline__ void fma_chunk32(float* acc, float w, const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  acc[0] = fmaf(w, a.x, acc[0]);
+  acc[1] = fmaf(w, a.y, acc[1]);
+  acc[2] = fmaf(w, a.z, acc[2]);
+  acc[3] = fmaf(w, a.w, acc[3]);
+  acc[4] = fmaf(w, b.x, acc[4]);
+  acc[5] = fmaf(w, b.y, acc[5]);
+  acc[6] = fmaf(w, b.z, acc[6]);
+  acc[7] = fmaf(w, b.w, acc[7]);
+}
+
 // small-parameter accumulators: [W_e (2F), b_e (F)] [b (F)] [w_r (2F+4)] [b_r (2)]
 __device__ __forceinline__ int sp_We(int F) { return 0; }
 __device__ __forceinline__ int sp_b(int F) { return 3 * F; }
 __device__ __forceinline__ int sp_wr(int F) { return 4 * F; }
 __device__ __forceinline__ int sp_br(int F) { return 6 * F + 4; }
+
+// FP32 row of layer l-1 of site v: the embedding row of its spin (l = 1), else H^{l-1}.
+__device__ __forceinline__ const float* tcb_hrow(const TcCtx& c, const float* Hs, int l, int v) {
+  return l == 1 ? c.emb + (c.spin[v] > 0 ? 0 : c.F) : Hs + ((size_t)(l - 2) * c.N + v) * c.ldy;
+}
+
+// X = [A_hat H^{l-1} ; H^{l-1}] row chunk (8 features of the message, mc < F/8, or of the
+// self term) of site v, FP32.
+__device__ __forceinline__ void tcb_xchunk(const TcCtx& c, const float* Hs, int l, int v, int mc, float* x) {
+  const int F8 = c.F / 8;
+  if (mc < F8) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = 0.f;
+    const int k0 = c.rp[v], k1 = c.rp[v + 1];
+    for (int k = k0; k < k1; ++k) fma_chunk32(x, c.wfs[k], tcb_hrow(c, Hs, l, __ldg(c.a->g.col + k)) + mc * 8);
+  } else {
+    const float* h = tcb_hrow(c, Hs, l, v) + (mc - F8) * 8;
+    const float4 a = *reinterpret_cast<const float4*>(h), b = *reinterpret_cast<const float4*>(h + 4);
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = a.z;
+    x[3] = a.w;
+    x[4] = b.x;
+    x[5] = b.y;
+    x[6] = b.z;
+    x[7] = b.w;
+  }
+}
+
+// Commit the MMAs issued by thread 0 and wait for them (bounded); false on timeout.
+__device__ __forceinline__ bool tcb_commit_wait(Unit& u, int* fail) {
+  if (threadIdx.x == 0) {
+    mma_commit(u.bar);
+    if (!mbar_wait_bounded(u.bar, u.phase)) {
+      *fail = 1;
+      atomicOr(&s_tc_status, 1);
+    }
+    u.phase ^= 1u;
+  }
+  __syncthreads();
+  tc_fence_after();
+  return *fail == 0;
+}
+
+// Forward of the configuration in c.spin with split operands: H^1..H^L into Hs (FP32).
+__device__ bool tcb_forward(const TcCtx& c, Unit& u, float* Hs) {
+  const int N = c.N, F = c.F, L = c.L, ldy = c.ldy, F8 = F / 8;
+  const uint32_t a_hi = smem_u32(u.A), a_lo = a_hi + 128u * 4u * (uint32_t)F, wt = smem_u32(c.Wt);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q4 = warp & 3, wg = warp >> 2;
+  for (int l = 1; l <= L; ++l) {
+    float* Hn = Hs + (size_t)(l - 1) * N * ldy;
+    for (int r0 = 0; r0 < N; r0 += 128) {
+      const int R = min(128, N - r0);
+      for (int idx = threadIdx.x; idx < R * 2 * F8; idx += blockDim.x) {
+        const int q = idx / (2 * F8), mc = idx - q * (2 * F8);
+        float x[8];
+        tcb_xchunk(c, Hs, l, r0 + q, mc, x);
+        uint4 hi, lo;
+        split_hi_lo(x, hi, lo);
+        *reinterpret_cast<uint4*>(u.A + canon(q, mc * 8, 2 * F)) = hi;
+        *reinterpret_cast<uint4*>(u.A + 128 * 4 * F + canon(q, mc * 8, 2 * F)) = lo;
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue_mma(u.tbase, a_hi, wt, 2 * F, F, false);
+        issue_mma(u.tbase, a_lo, wt, 2 * F, F, true);
+      }
+      if (!tcb_commit_wait(u, c.fail)) return false;
+      const int q = q4 * 32 + lane;
+      for (int ch = wg; ch < F8; ch += u.nwg) {
+        float v[8];
+        tmem_ld8(u.tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ch * 8), v);
+        if (q < R) {
+          float* o = Hn + (size_t)(r0 + q) * ldy + ch * 8;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = tanhf(v[i] + c.bias[ch * 8 + i]);
+          reinterpret_cast<float4*>(o)[0] = make_float4(v[0], v[1], v[2], v[3]);
+          reinterpret_cast<float4*>(o)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  return true;
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1739,7 +1869,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   c.sdbl = (double*)(smem + b.lay.odbl);
   c.region = b.region_in_smem ? smem + b.lay.oregion : b.gregion + (size_t)blockIdx.x * b.lay.region_bytes;
   c.fail = &s_fail;
-  const int F = c.F, N = c.N, L = c.L, ldh = c.ldh, ldy = c.ldy;
+  const int F = c.F, N = c.N, L = c.L, ldy = c.ldy;
   const int F8 = F / 8, F2 = 2 * F;
   const Dims& m = b.m;
   const float* th = b.theta;
@@ -1749,9 +1879,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   unsigned char* Xt = smem + a.oXt;
   unsigned char* dYt = smem + a.odYt;
   double* sp = (double*)(smem + a.osp);
+  float* Hs = (float*)(c.region + a.rH);
   float* Gs = (float*)(c.region + a.rG);
   float* dx = (float*)(c.region + a.rdx);
   const int nsp = 6 * F + 6;
+  const int packed = a.xt_packed;
+  // X^T lo rows: below the hi rows in the same tile, or in a second tile
+  unsigned char* Xlo = packed ? Xt : Xt + 128 * 128 * 2;
+  const int xlo_row = packed ? F2 : 0;
+  unsigned char* dYlo = dYt + F * 128 * 2;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -1764,10 +1900,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   const float* W = th + m.oW;
   for (int i = threadIdx.x; i < F * F2; i += blockDim.x) {
     const int n = i / F2, k = i % F2;  // forward B: W^T (n = output, k = input)
-    unsigned char* p = (unsigned char*)c.Wt + (size_t)(n >> 3) * (32 * F) + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+    const __nv_bfloat16 w = __float2bfloat16_rn(W[(size_t)k * F + n]);
+    *reinterpret_cast<__nv_bfloat16*>((unsigned char*)c.Wt + canon(n, k, F2)) = w;
     // backward dX: B = W (n' = input feature k, k' = output feature n), K = F
-    *reinterpret_cast<__nv_bfloat16*>(Wb + canon(k, n, F)) = __float2bfloat16_rn(W[(size_t)k * F + n]);
+    *reinterpret_cast<__nv_bfloat16*>(Wb + canon(k, n, F)) = w;
   }
   for (int i = threadIdx.x; i < F; i += blockDim.x) c.bias[i] = th[m.ob + i];
   for (int i = threadIdx.x; i < 2 * F; i += blockDim.x) c.emb[i] = tanhf(th[m.oWe + i] + th[m.obe + i % F]);
@@ -1776,8 +1912,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   for (int i = threadIdx.x; i <= c.N; i += blockDim.x) ((int*)c.rp)[i] = __ldg(b.g.row_ptr + i);
   for (int i = threadIdx.x; i < 2 * c.E; i += blockDim.x) ((float*)c.wfs)[i] = __ldg(b.g.wf + i);
   for (int i = threadIdx.x; i < nsp; i += blockDim.x) sp[i] = 0.0;
-  // X^T rows 2F..127 stay zero (M padded to 128)
-  for (int i = threadIdx.x; i < 128 * 128 * 2 / 16; i += blockDim.x) reinterpret_cast<uint4*>(Xt)[i] = make_uint4(0, 0, 0, 0);
+  // rows of X^T past the stacked hi and lo rows stay zero (M is 128)
+  for (int i = threadIdx.x; i < (packed ? 1 : 2) * 128 * 128 * 2 / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(Xt)[i] = make_uint4(0, 0, 0, 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1793,6 +1930,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   u.tbase = tmem;
   u.bar = bars;
   u.phase = 0;
+  const uint32_t a_hi = smem_u32(u.A), a_lo = a_hi + 128u * 2u * (uint32_t)F;  // dY rows, K = F
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q4 = warp & 3, wg = warp >> 2;
   bool dw_started = false;  // meaningful in thread 0
   bool ok = true;
@@ -1800,21 +1938,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   for (int64_t bi = blockIdx.x; bi < b.B && ok; bi += gridDim.x) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) c.spin[i] = b.spins[bi * N + i];
     __syncthreads();
-    ok = tc_forward(c, u);
+    ok = tcb_forward(c, u, Hs);
     if (!ok) break;
     ++nsamples;
     const float c0 = (float)a.cot[2 * bi], c1 = (float)a.cot[2 * bi + 1];
     // readout: d w_r[f] += cot z_f with z = sum_v [H^L_v ; onehot_v]; d b_r += cot.  The
     // column sums over sites run on the whole block: P interleaved site strides per feature,
     // their FP32 partials (in the free dX buffer) added in a fixed order
-    const float* seL = cacheY(c, L);
+    const float* HL = Hs + (size_t)(L - 1) * N * ldy;
     const int P = min((int)blockDim.x / F, N), fcol = threadIdx.x % F, part = threadIdx.x / F;
     if (part < P) {
       float zz = 0.f;
-      for (int v = part; v < N; v += P) {
-        const float se = seL[(size_t)v * ldy + fcol], e = fabsf(se);
-        zz += copysignf(__fdividef(1.f - e, 1.f + e), se);
-      }
+      for (int v = part; v < N; v += P) zz += HL[(size_t)v * ldy + fcol];
       dx[part * F + fcol] = zz;
     }
     __syncthreads();
@@ -1843,14 +1978,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
     }
     __syncthreads();
     for (int l = L; l >= 1 && ok; --l) {
-      const float* se = cacheY(c, l);
-      const __nv_bfloat16* hp = cache16(c, l - 1);
+      const float* Hl = Hs + (size_t)(l - 1) * N * ldy;
       // db += sum_v dY^l_v (block-wide column sums as for the readout; dX is free here)
       if (part < P) {
         float sum = 0.f;
         for (int v = part; v < N; v += P) {
-          const float e = fabsf(se[(size_t)v * ldy + fcol]), ope = 1.f + e;
-          sum += Gs[(size_t)v * F + fcol] * __fdividef(4.f * e, ope * ope);
+          const float h = Hl[(size_t)v * ldy + fcol];
+          sum += Gs[(size_t)v * F + fcol] * fmaf(-h, h, 1.f);
         }
         dx[part * F + fcol] = sum;
       }
@@ -1862,69 +1996,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
       }
       for (int c0s = 0; c0s < N && ok; c0s += 128) {
         const int ns = min(128, N - c0s);
-        // dY rows of the chunk: as the A operand of dX (rows, K = F) and, transposed, as the
-        // B operand of dW (rows = output features, K = sites); zeros past the last site
+        // dY rows of the chunk, hi and lo: as the A operands of dX (rows, K = F) and,
+        // transposed, as the B operands of dW (rows = output features, K = sites); zeros past
+        // the last site
         for (int idx = threadIdx.x; idx < 128 * F8; idx += blockDim.x) {
           const int r = idx / F8, ch = idx - r * F8, v = c0s + r;
           float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
           if (r < ns) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const float e = fabsf(se[(size_t)v * ldy + ch * 8 + i]), ope = 1.f + e;
-              d[i] = Gs[(size_t)v * F + ch * 8 + i] * __fdividef(4.f * e, ope * ope);
+              const float h = Hl[(size_t)v * ldy + ch * 8 + i];
+              d[i] = Gs[(size_t)v * F + ch * 8 + i] * fmaf(-h, h, 1.f);
             }
           }
-          uint4 w;
-          w.x = pack_bf16(d[0], d[1]);
-          w.y = pack_bf16(d[2], d[3]);
-          w.z = pack_bf16(d[4], d[5]);
-          w.w = pack_bf16(d[6], d[7]);
-          *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = w;
+          uint4 hi, lo;
+          split_hi_lo(d, hi, lo);
+          *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = hi;
+          *reinterpret_cast<uint4*>(u.A + 128 * 2 * F + canon(r, ch * 8, F)) = lo;
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            *reinterpret_cast<__nv_bfloat16*>(dYt + canon(ch * 8 + i, r, 128)) = __float2bfloat16_rn(d[i]);
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat16 h, l2;
+            split1(d[i], h, l2);
+            *reinterpret_cast<__nv_bfloat16*>(dYt + canon(ch * 8 + i, r, 128)) = h;
+            *reinterpret_cast<__nv_bfloat16*>(dYlo + canon(ch * 8 + i, r, 128)) = l2;
+          }
         }
-        // X = [A_hat H^{l-1} ; H^{l-1}] of the chunk's sites, transposed (rows = input features)
+        // X = [A_hat H^{l-1} ; H^{l-1}] of the chunk's sites, transposed (rows = input
+        // features), hi and lo
         for (int idx = threadIdx.x; idx < 128 * 2 * F8; idx += blockDim.x) {
           const int r = idx / (2 * F8), mc = idx - r * (2 * F8), v = c0s + r;
           float x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (r < ns) {
-            if (mc < F8) {
-              const int k0 = c.rp[v], k1 = c.rp[v + 1];
-              for (int k = k0; k < k1; ++k) fma_chunk(x, c.wfs[k], hp + (size_t)__ldg(b.g.col + k) * ldh + mc * 8);
-            } else {
-              const uint4 h = *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + (mc - F8) * 8);
-              x[0] = bf16lo(h.x);
-              x[1] = bf16hi(h.x);
-              x[2] = bf16lo(h.y);
-              x[3] = bf16hi(h.y);
-              x[4] = bf16lo(h.z);
-              x[5] = bf16hi(h.z);
-              x[6] = bf16lo(h.w);
-              x[7] = bf16hi(h.w);
-            }
-          }
+          if (r < ns) tcb_xchunk(c, Hs, l, v, mc, x);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            *reinterpret_cast<__nv_bfloat16*>(Xt + canon(mc * 8 + i, r, 128)) = __float2bfloat16_rn(x[i]);
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat16 h, l2;
+            split1(x[i], h, l2);
+            *reinterpret_cast<__nv_bfloat16*>(Xt + canon(mc * 8 + i, r, 128)) = h;
+            *reinterpret_cast<__nv_bfloat16*>(Xlo + canon(xlo_row + mc * 8 + i, r, 128)) = l2;
+          }
         }
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
           tc_fence_after();
-          issue_mma(t_dw, smem_u32(Xt), smem_u32(dYt), 128, F, dw_started);
+          const uint32_t xt = smem_u32(Xt), yh = smem_u32(dYt), yl = smem_u32(dYlo);
+          // dW: packed tile rows [0, 2F) = X_hi^T (dY_hi + dY_lo), rows [2F, 4F) = X_lo^T (dY_hi
+          // + dY_lo), summed at the end; separate tiles: X_hi^T dY_hi + X_hi^T dY_lo + X_lo^T dY_hi
+          issue_mma(t_dw, xt, yh, 128, F, dw_started);
+          issue_mma(t_dw, xt, yl, 128, F, true);
+          if (!packed) issue_mma(t_dw, smem_u32(Xlo), yh, 128, F, true);
           dw_started = true;
-          issue_mma(t_dx, smem_u32(u.A), smem_u32(Wb), F, F2, false);
-          mma_commit(u.bar);
-          if (!mbar_wait_bounded(u.bar, u.phase)) {
-            s_fail = 1;
-            atomicOr(&s_tc_status, 1);
-          }
-          u.phase ^= 1u;
+          issue_mma(t_dx, a_hi, smem_u32(Wb), F, F2, false);
+          issue_mma(t_dx, a_lo, smem_u32(Wb), F, F2, true);
         }
-        __syncthreads();
-        tc_fence_after();
-        if (s_fail) {
+        if (!tcb_commit_wait(u, c.fail)) {
           ok = false;
           break;
         }
@@ -1946,25 +2071,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
       // G^{l-1}_v = dX_v[F:] + sum_u A_hat_vu dX_u[:F]
       for (int idx = threadIdx.x; idx < N * F8; idx += blockDim.x) {
         const int v = idx / F8, ch = idx - v * F8;
+        float acc[8];
         const float4* sf = reinterpret_cast<const float4*>(dx + (size_t)v * F2 + F + ch * 8);
-        float4 a0 = sf[0], a1 = sf[1];
+        const float4 s0 = sf[0], s1 = sf[1];
+        acc[0] = s0.x;
+        acc[1] = s0.y;
+        acc[2] = s0.z;
+        acc[3] = s0.w;
+        acc[4] = s1.x;
+        acc[5] = s1.y;
+        acc[6] = s1.z;
+        acc[7] = s1.w;
         const int k0 = c.rp[v], k1 = c.rp[v + 1];
-        for (int k = k0; k < k1; ++k) {
-          const float w = c.wfs[k];
-          const float4* mu = reinterpret_cast<const float4*>(dx + (size_t)__ldg(b.g.col + k) * F2 + ch * 8);
-          const float4 m0 = mu[0], m1 = mu[1];
-          a0.x += w * m0.x;
-          a0.y += w * m0.y;
-          a0.z += w * m0.z;
-          a0.w += w * m0.w;
-          a1.x += w * m1.x;
-          a1.y += w * m1.y;
-          a1.z += w * m1.z;
-          a1.w += w * m1.w;
-        }
+        for (int k = k0; k < k1; ++k) fma_chunk32(acc, c.wfs[k], dx + (size_t)__ldg(b.g.col + k) * F2 + ch * 8);
         float4* go = reinterpret_cast<float4*>(Gs + (size_t)v * F + ch * 8);
-        go[0] = a0;
-        go[1] = a1;
+        go[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        go[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
       __syncthreads();
     }
@@ -1990,23 +2112,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
         sd += dx[(P + q) * F + f];
       }
       const float eu = c.emb[f], ed = c.emb[F + f];
-      const double du = (double)(su * (1.f - eu * eu)), dd = (double)(sd * (1.f - ed * ed));
+      const double du = (double)(su * fmaf(-eu, eu, 1.f)), dd = (double)(sd * fmaf(-ed, ed, 1.f));
       sp[sp_We(F) + f] += du;
       sp[sp_We(F) + F + f] += dd;
       sp[sp_We(F) + 2 * F + f] += du + dd;
     }
     __syncthreads();
   }
-  // partials: dW from TMEM (lanes = input features), the rest from the FP64 accumulators
+  // partials: dW from TMEM (lanes = rows of X^T: input features, hi then lo when packed), the
+  // rest from the FP64 accumulators
   double* part = a.partial + (size_t)blockIdx.x * m.P;
   if (ok) {
     const int mrow = q4 * 32 + lane;
+    float* lo_rows = dx;  // [2F][F] the packed lo rows' sums, added to the hi rows below
+    for (int ch = wg; ch < F8; ch += u.nwg) {
+      float v8[8];
+      tmem_ld8(t_dw + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ch * 8), v8);
+      if (packed && mrow >= F2 && mrow < 2 * F2)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) lo_rows[(size_t)(mrow - F2) * F + ch * 8 + i] = v8[i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     for (int ch = wg; ch < F8; ch += u.nwg) {
       float v8[8];
       tmem_ld8(t_dw + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ch * 8), v8);
       if (mrow < F2)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) part[m.oW + (size_t)mrow * F + ch * 8 + i] = nsamples > 0 ? (double)v8[i] : 0.0;
+        for (int i = 0; i < 8; ++i) {
+          const double lo = packed ? (double)lo_rows[(size_t)mrow * F + ch * 8 + i] : 0.0;
+          part[m.oW + (size_t)mrow * F + ch * 8 + i] = nsamples > 0 ? (double)v8[i] + lo : 0.0;
+        }
     }
     for (int f = threadIdx.x; f < 3 * F; f += blockDim.x) part[m.oWe + f] = sp[sp_We(F) + f];  // W_e, b_e
     for (int f = threadIdx.x; f < F; f += blockDim.x) part[m.ob + f] = sp[sp_b(F) + f];
@@ -2342,12 +2479,15 @@ static void tcb_layout(const Dims& m, int region_in_smem, TcbArgs* A) {
   t->T = 1;
   t->units = 1;
   t->G = 1;
-  t->a_unit = 128 * 2 * F * 2;
+  // A operands: the forward's hi and lo tiles of 128 rows x 2F (the backward's dY tiles,
+  // 128 x F each, use the same space)
+  t->a_unit = 2 * 128 * 2 * F * 2;
+  A->xt_packed = 4 * F <= 128;
   t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
   A->oWb = take((uint64_t)2 * F * F * 2, 1024);
   t->oA = take(t->a_unit, 1024);
-  A->oXt = take(128 * 128 * 2, 1024);
-  A->odYt = take((uint64_t)F * 128 * 2, 1024);
+  A->oXt = take((uint64_t)(A->xt_packed ? 1 : 2) * 128 * 128 * 2, 1024);
+  A->odYt = take((uint64_t)2 * F * 128 * 2, 1024);
   t->obias = take(F * 4, 16);
   t->oemb = take(2 * F * 4, 16);
   t->owr = take((F + 2) * 2 * 4, 16);
@@ -2367,11 +2507,11 @@ static void tcb_layout(const Dims& m, int region_in_smem, TcbArgs* A) {
     r += bytes;
     return x;
   };
-  const uint64_t ldh = F + 8, ldy = F + 4;
-  t->rY = rtake((uint64_t)L * N * ldy * 4);
-  t->rcache16 = rtake((uint64_t)L * N * ldh * 2);
+  const uint64_t ldy = F + 4;
+  A->rH = rtake((uint64_t)L * N * ldy * 4);
   A->rG = rtake((uint64_t)N * F * 4);
-  A->rdx = rtake((uint64_t)N * 2 * F * 4);
+  // dX rows; also the scratch of the column sums and of the stacked lo rows of dW
+  A->rdx = rtake((uint64_t)(N > F ? N : F) * 2 * F * 4);
   t->region_bytes = (r + 255) / 256 * 256;
   t->oregion = region_in_smem ? take(t->region_bytes, 16) : 0;
   t->smem_total = (uint32_t)o;
@@ -2425,7 +2565,11 @@ gna_status tcb_workspace(const gna_graph* g, const Dims& m, int64_t B, size_t* b
   return GNA_OK;
 }
 
-gna_status tcb_run(const TcbCall& call, void* ws, size_t ws_bytes, cudaStream_t stream) {
+// Launches the backward with its per-CTA partials (and per-CTA regions when they do not fit
+// in shared memory) in ws.  max_bytes > 0: ws is a fixed array of that size and the grid is
+// reduced to fit it (a single CTA that does not fit is GNA_ERR_WORKSPACE); otherwise ws must
+// hold tcb_workspace() bytes.
+static gna_status tcb_launch(const TcbCall& call, void* ws, size_t ws_bytes, size_t max_bytes, cudaStream_t stream) {
   if (call.B == 0) {
     GNA_CUDA_TRY(cudaMemsetAsync(call.grad, 0, (size_t)call.m.P * sizeof(double), stream));
     return GNA_OK;
@@ -2433,6 +2577,16 @@ gna_status tcb_run(const TcbCall& call, void* ws, size_t ws_bytes, cudaStream_t 
   TcbPlan p;
   gna_status st = tcb_plan(call.g, call.m, call.B, &p);
   if (st != GNA_OK) return st;
+  if (max_bytes > 0) {
+    const size_t region = p.a.base.region_in_smem ? 0 : (size_t)p.a.base.lay.region_bytes;
+    const size_t per_cta = (size_t)call.m.P * sizeof(double) + region;
+    int64_t grid = (int64_t)((max_bytes - 512) / per_cta);  // two 256-byte alignment pads
+    if (grid < 1) return GNA_ERR_WORKSPACE;
+    if (grid < p.grid) p.grid = (int)grid;
+    p.partial_bytes = align_up((size_t)p.grid * call.m.P * sizeof(double));
+    p.ws_bytes = p.partial_bytes + align_up((size_t)p.grid * region);
+    ws_bytes = max_bytes;
+  }
   if (ws_bytes < p.ws_bytes || !ws) return GNA_ERR_WORKSPACE;
   TcbArgs& a = p.a;
   a.base.g = call.g->d;
@@ -2449,6 +2603,14 @@ gna_status tcb_run(const TcbCall& call, void* ws, size_t ws_bytes, cudaStream_t 
   k_tcb_reduce<<<(call.m.P + 255) / 256, 256, 0, stream>>>(a.partial, p.grid, call.m.P, call.grad);
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
+}
+
+gna_status tcb_run(const TcbCall& call, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  return tcb_launch(call, ws, ws_bytes, 0, stream);
+}
+
+gna_status tcb_run_fixed(const TcbCall& call, void* scratch, size_t scratch_bytes, cudaStream_t stream) {
+  return tcb_launch(call, scratch, scratch_bytes, scratch_bytes, stream);
 }
 
 gna_status tc_read_status(int* flags, int clear) {

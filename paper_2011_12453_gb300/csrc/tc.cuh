@@ -49,6 +49,8 @@ struct TcbCall {
 gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes);
 gna_status tcb_workspace(const gna_graph* g, const Dims& m, int64_t B, size_t* bytes);
 gna_status tcb_run(const TcbCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
+// Same backward with its scratch in a fixed array of scratch_bytes (the grid is reduced to fit).
+gna_status tcb_run_fixed(const TcbCall& c, void* scratch, size_t scratch_bytes, cudaStream_t stream);
 gna_status tcm_workspace(const gna_graph* g, const Dims& m, int64_t C, size_t* bytes);
 gna_status tcm_run(const TcmCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_run(const TcCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);

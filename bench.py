@@ -362,7 +362,7 @@ def run_ours(a):
             gna.workspace_size(graph, gna.Model(F, L, gna.PREC_BF16), gna.OP_ELOC_INCR, Bn)
         except gna.GnaError:
             prec_name = "fp32"
-    prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32}[prec_name]
+    prec = {"bf16": gna.PREC_BF16, "bf16x2": gna.PREC_BF16X2, "fp32": gna.PREC_FP32}[prec_name]
     model = gna.Model(F, L, prec)
     model32 = gna.Model(F, L, gna.PREC_FP32)
     model_bwd = model32 if a.backward_prec == "fp32" else model
@@ -493,7 +493,7 @@ def run_ours(a):
     alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     t_sweep = float(np.median(ph[:, 0]))
     if t_sweep >= K * t_incr:
-        if prec == gna.PREC_BF16 and prop is None:
+        if prec in (gna.PREC_BF16, gna.PREC_BF16X2) and prop is None:
             roof = {"bound": "tensor", "achieved": fl_sweep / (t_sweep / 1000.0) / 1e12,
                     "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                     "kernel": "k_tc_metro (gna_metropolis_sweep, %d sweeps, BF16 tcgen05)" % S,
@@ -504,7 +504,7 @@ def run_ours(a):
                     "unit": "TFLOP/s", "kernel": "k_metro_warp (gna_metropolis_sweep, %d sweeps)" % S,
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz (FP32 difference propagation)",
                     "flops_per_launch": fl_sweep, "traffic": None}
-    elif prec == gna.PREC_BF16:
+    elif prec in (gna.PREC_BF16, gna.PREC_BF16X2):
         roof = {"bound": "tensor", "achieved": fl_incr / (t_incr / 1000.0) / 1e12,
                 "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                 "kernel": "k_tc (gna_local_energy incremental, BF16 tcgen05)",
@@ -565,7 +565,7 @@ def run_only(a):
     wl = a.wl
     g = make_graph(wl)
     F, L, C = wl["F"], wl["L"], wl["chains"]
-    prec = {"bf16": gna.PREC_BF16, "fp32": gna.PREC_FP32, "auto": gna.PREC_BF16}[a.prec]
+    prec = {"bf16": gna.PREC_BF16, "bf16x2": gna.PREC_BF16X2, "fp32": gna.PREC_FP32, "auto": gna.PREC_BF16}[a.prec]
     graph = gna.Graph.from_workload(g, L)
     model = gna.Model(F, L, prec)
     model32 = gna.Model(F, L, gna.PREC_FP32)

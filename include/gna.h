@@ -61,15 +61,20 @@ typedef int32_t gna_status;
 
 /* Arithmetic of a call.  FP64: float64 everywhere (parity path).  FP32: float32
  * features, GEMMs and ratios.  BF16: the node-feature GEMM operands in bfloat16 on the
- * tensor cores with float32 accumulation; everything else as FP32.  Reductions across
- * samples (energies, weights, gradients) are float64 in every mode. */
-typedef enum { GNA_PREC_FP64 = 0, GNA_PREC_FP32 = 1, GNA_PREC_BF16 = 2 } gna_prec;
+ * tensor cores with float32 accumulation; everything else as FP32.  BF16X2: the same
+ * tensor-core GEMMs with every float32 operand x carried as two bfloat16 values,
+ * hi = bf16(x) and lo = bf16(x - hi) (about 16 significant bits), both multiplied and
+ * accumulated in float32; feature rows in float32 and tanh to float32 accuracy.  W is a
+ * bfloat16 model parameter in both tensor-core modes (the float32 theta is rounded).  The
+ * backward (gna_backward) always splits its operands; the sampler runs BF16 for both.
+ * Reductions across samples (energies, weights, gradients) are float64 in every mode. */
+typedef enum { GNA_PREC_FP64 = 0, GNA_PREC_FP32 = 1, GNA_PREC_BF16 = 2, GNA_PREC_BF16X2 = 3 } gna_prec;
 
 /* Nonlinearity f of Eq. (gcn), also applied after the embedding's dense layer.
  * TANH: tanh elementwise.  RELU_LN: the GNA section's f, ReLU followed by a layer
  * normalisation over the F features of each site's row, (r - mean r)/sqrt(var r + 1e-6)
  * with r = max(y, 0) and no affine part (the paper gives neither eps nor an affine part).
- * RELU_LN runs at GNA_PREC_FP64 / GNA_PREC_FP32 (calls with GNA_PREC_BF16 return
+ * RELU_LN runs at GNA_PREC_FP64 / GNA_PREC_FP32 (calls with GNA_PREC_BF16 or BF16X2 return
  * GNA_ERR_UNSUPPORTED); its Metropolis sweeps take the one-chain-per-CTA kernel. */
 typedef enum { GNA_ACT_TANH = 0, GNA_ACT_RELU_LN = 1 } gna_act;
 
@@ -92,8 +97,8 @@ typedef enum {
 
 /* Model description (Eq. gcn).  F = embedding width, L = number of GCN layers,
  * shared_weights = 1 for one (W, b) reused by all layers (the paper's choice),
- * 0 for one (W, b) per layer.  Limits of this build: 1 <= F <= 64 (BF16: F a multiple
- * of 16), 0 <= L <= 8, L <= the graph's max_layers. */
+ * 0 for one (W, b) per layer.  Limits of this build: 1 <= F <= 64 (BF16, BF16X2: F a
+ * multiple of 16 and shared weights), 0 <= L <= 8, L <= the graph's max_layers. */
 typedef struct {
   int32_t F;
   int32_t L;
@@ -227,7 +232,8 @@ GNA_API gna_status gna_local_energy(const gna_graph* g, const gna_model_desc* d,
  *                accepted, value, kind) with value = Re Delta (plain sampler) or the log
  *                acceptance ratio (with a proposal network), NaN when nothing was
  *                proposed, and kind 1 = plain bond, 2 = network move
- * Incremental ratios are computed in d->prec (BF16 runs the FP32 sampler). */
+ * Incremental ratios are computed in d->prec; BF16 and BF16X2 models with plain moves run
+ * the BF16 tensor-core sampler, with a proposal network the FP32 warp sampler. */
 GNA_API gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_desc* d,
                                 const void* theta, int8_t* chain_spins, int64_t C,
                                 int32_t n_sweeps, int32_t record_every, uint64_t seed,

@@ -37,21 +37,25 @@ gna_status device_info(DeviceInfo* out) {
   return GNA_OK;
 }
 
+// Descriptors whose GEMMs run on the tensor cores: BF16 and BF16X2 (split operands).
+static bool tensor_prec(const gna_model_desc* d) { return d->prec == GNA_PREC_BF16 || d->prec == GNA_PREC_BF16X2; }
+static int split_prec(const gna_model_desc* d) { return d->prec == GNA_PREC_BF16X2 ? 1 : 0; }
+
 static bool desc_ok(const gna_model_desc* d) {
   if (!d) return false;
   if (d->F < 1 || d->F > kMaxF) return false;
   if (d->L < 0 || d->L > kMaxL) return false;
   if (d->act != GNA_ACT_TANH && d->act != GNA_ACT_RELU_LN) return false;
-  if (d->prec < GNA_PREC_FP64 || d->prec > GNA_PREC_BF16) return false;
+  if (d->prec < GNA_PREC_FP64 || d->prec > GNA_PREC_BF16X2) return false;
   if (d->shared_weights != 0 && d->shared_weights != 1) return false;
-  if (d->prec == GNA_PREC_BF16 && d->F % 16 != 0) return false;
+  if (tensor_prec(d) && d->F % 16 != 0) return false;
   return true;
 }
 
 static gna_status check_gd(const gna_graph* g, const gna_model_desc* d) {
   if (!g || !desc_ok(d)) return GNA_ERR_INVALID_ARG;
   // ReLU + layer norm runs on the float64 / float32 SIMT kernels only
-  if (d->act == GNA_ACT_RELU_LN && d->prec == GNA_PREC_BF16) return GNA_ERR_UNSUPPORTED;
+  if (d->act == GNA_ACT_RELU_LN && tensor_prec(d)) return GNA_ERR_UNSUPPORTED;
   if (d->L > g->d.Lmax) return GNA_ERR_INVALID_ARG;
   int dev = 0;
   GNA_CUDA_TRY(cudaGetDevice(&dev));
@@ -59,8 +63,8 @@ static gna_status check_gd(const gna_graph* g, const gna_model_desc* d) {
   return GNA_OK;
 }
 
-// Arithmetic of the SIMT kernels for a descriptor: BF16 descriptors run their
-// non-tensor-core steps (sampler, backward) in float32.
+// Arithmetic of the SIMT kernels for a descriptor: BF16 / BF16X2 descriptors run their
+// non-tensor-core steps in float32.
 static int simt_prec(const gna_model_desc* d) { return d->prec == GNA_PREC_FP64 ? GNA_PREC_FP64 : GNA_PREC_FP32; }
 
 static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int op, int64_t B, size_t* bytes);
@@ -116,15 +120,15 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
   const int sp = simt_prec(d);
   switch (op) {
     case GNA_OP_FORWARD:
-      if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_FWD, B, bytes);
+      if (tensor_prec(d)) return tc_workspace(g, m, TC_FWD, B, bytes, split_prec(d));
       return simt_workspace(g, m, sp, 0, B, bytes);
     case GNA_OP_LOCAL_ENERGY_FULL:
       return simt_workspace(g, m, sp, 1, B, bytes);
     case GNA_OP_LOCAL_ENERGY_INCREMENTAL:
-      if (d->prec == GNA_PREC_BF16) return tc_workspace(g, m, TC_ELOC, B, bytes);
+      if (tensor_prec(d)) return tc_workspace(g, m, TC_ELOC, B, bytes, split_prec(d));
       return simt_workspace(g, m, sp, 2, B, bytes);
     case GNA_OP_METROPOLIS: {
-      if (d->prec == GNA_PREC_BF16) {
+      if (tensor_prec(d)) {
         gna_status st = tcm_workspace(g, m, B, bytes);
         if (st != GNA_ERR_UNSUPPORTED) return st;
       }
@@ -144,7 +148,7 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       return simt_workspace(g, m, sp, 5, B, bytes);
     }
     case GNA_OP_BACKWARD:
-      if (d->prec == GNA_PREC_BF16) {
+      if (tensor_prec(d)) {
         gna_status st = tcb_workspace(g, m, B, bytes);
         if (st != GNA_ERR_UNSUPPORTED) return st;
       }
@@ -199,8 +203,8 @@ extern "C" gna_status gna_forward(const gna_graph* g, const gna_model_desc* d, c
   st = check_ws(g, d, GNA_OP_FORWARD, B, workspace, workspace_bytes);
   if (st != GNA_OK) return st;
   const Dims m = make_dims(g, d);
-  if (d->prec == GNA_PREC_BF16) {
-    TcCall tc{g, m, TC_FWD, (const float*)theta, spins, B, logpsi, nullptr, nullptr};
+  if (tensor_prec(d)) {
+    TcCall tc{g, m, TC_FWD, (const float*)theta, spins, B, logpsi, nullptr, nullptr, split_prec(d)};
     return tc_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
   }
   SimtCall sc{};
@@ -228,8 +232,8 @@ extern "C" gna_status gna_local_energy(const gna_graph* g, const gna_model_desc*
   st = check_ws(g, d, op, B, workspace, workspace_bytes);
   if (st != GNA_OK) return st;
   const Dims m = make_dims(g, d);
-  if (d->prec == GNA_PREC_BF16 && mode == GNA_ELOC_INCREMENTAL) {
-    TcCall tc{g, m, TC_ELOC, (const float*)theta, spins, B, nullptr, eloc, dlogpsi_bonds};
+  if (tensor_prec(d) && mode == GNA_ELOC_INCREMENTAL) {
+    TcCall tc{g, m, TC_ELOC, (const float*)theta, spins, B, nullptr, eloc, dlogpsi_bonds, split_prec(d)};
     return tc_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
   }
   SimtCall sc{};
@@ -280,7 +284,7 @@ extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_d
   // BF16 models, plain moves: the tensor-core sampler; otherwise the warp-per-chain sampler
   // when the model fits it, else one chain per CTA
   size_t need = 0;
-  if (d->prec == GNA_PREC_BF16 && !proposal_params && tcm_workspace(g, sc.m, C, &need) == GNA_OK) {
+  if (tensor_prec(d) && !proposal_params && tcm_workspace(g, sc.m, C, &need) == GNA_OK) {
     TcmCall tc{g, sc.m, (const float*)theta, chain_spins, C, n_sweeps, record_every, seed, step0,
                samples_out, logpsi_out, n_accepted, trace};
     return tcm_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
@@ -305,7 +309,7 @@ extern "C" gna_status gna_backward(const gna_graph* g, const gna_model_desc* d, 
   if (st != GNA_OK) return st;
   // BF16 models: the tensor-core backward when the model fits it
   size_t need = 0;
-  if (d->prec == GNA_PREC_BF16 && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
+  if (tensor_prec(d) && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
     TcbCall tc{g, make_dims(g, d), (const float*)theta, spins, B, cot, grad};
     return tcb_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
   }
@@ -330,7 +334,7 @@ extern "C" gna_status gna_backward_static(const gna_graph* g, const gna_model_de
   if (!theta || !grad || (B > 0 && (!spins || !cot))) return GNA_ERR_INVALID_ARG;
   // BF16 models: the tensor-core backward of gna_backward, with its scratch in the fixed array
   size_t need = 0;
-  if (d->prec == GNA_PREC_BF16 && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
+  if (tensor_prec(d) && tcb_workspace(g, make_dims(g, d), B, &need) == GNA_OK) {
     void* base = nullptr;
     size_t bytes = 0;
     st = static_scratch(&base, &bytes);

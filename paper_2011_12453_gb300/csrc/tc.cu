@@ -232,6 +232,8 @@ struct TcLayout {
   uint64_t rcache16, rY, rnew16, rpart, region_bytes;
   uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
   int T;                          // A tiles per unit (TMEM holds T accumulators of F columns per unit)
+  int split;                      // 1: operands as hi + lo BF16 pairs, FP32 feature rows
+  uint32_t lo_off;                // split: bytes from a unit's hi tiles to its lo tiles
   int units;                      // bond-group units per CTA
   int G;                          // bonds per group (per unit)
   uint32_t a_unit;                // bytes of one unit's A tiles
@@ -263,7 +265,7 @@ struct TcArgs {
 // the local energy with four units: 33.6 ms instead of 30.8).  One 128-row tile per unit
 // and pass: the shared memory goes to larger bond groups instead (measured at Kagome 108,
 // F = 32: two tiles and 4 bonds per group 43.3 ms, one tile and 6 bonds 41.9 ms).
-__host__ inline int tc_units(int F) { return F <= 32 ? 2 : 4; }
+__host__ inline int tc_units(int F, int split = 0) { return F <= 32 || split ? 2 : 4; }
 __host__ inline int tcm_units(int F) { return F <= 16 ? 2 : 4; }
 __host__ inline int tc_tiles_per_unit(int) { return 1; }
 
@@ -296,7 +298,7 @@ __host__ inline void tc_stage_layout(const Dims& m, const int* maxball, int maxs
 // alias_new16: the group rows' dH layers share the space of the BF16 layer cache, which
 // only the forward reads (the incremental step needs the pre-activations alone).
 __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, int G, int region_in_smem,
-                               int alias_new16, TcLayout* t) {
+                               int alias_new16, TcLayout* t, int split = 0) {
   const int F = m.F, N = m.N, L = m.L;
   uint64_t o = 0;
   auto take = [&](uint64_t bytes, uint64_t align) {
@@ -306,10 +308,12 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
     return (uint32_t)r;
   };
   t->T = tc_tiles_per_unit(F);
-  t->units = tc_units(F);
+  t->units = tc_units(F, split);
+  t->split = split;
   const int U = t->units;
   t->G = G;
-  t->a_unit = (uint32_t)t->T * 128 * 2 * F * 2;
+  t->lo_off = (uint32_t)t->T * 128 * 2 * F * 2;
+  t->a_unit = t->lo_off * (split ? 2 : 1);
   t->oWt = take((uint64_t)F * 2 * F * 2, 1024);
   t->oA = take((uint64_t)U * t->a_unit, 1024);
   t->obias = take(F * 4, 16);
@@ -333,14 +337,16 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
     return x;
   };
   const uint64_t ldh = F + 8, ldy = F + 4;  // padded row strides (BF16 rows, FP32 rows)
+  // feature rows of the layer cache and of the dH rows: BF16, or FP32 when split
+  const uint64_t row_bytes = split ? ldy * 4 : ldh * 2;
   t->rY = rtake((uint64_t)L * N * ldy * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
   uint64_t n16 = 0;
   for (int l = 0; l < L; ++l) {
     t->new16_off[l] = n16;
-    n16 += (uint64_t)G * maxball[l] * ldh * 2;
+    n16 += (uint64_t)G * maxball[l] * row_bytes;
   }
   t->new16_unit = (n16 + 15) / 16 * 16;
-  const uint64_t cache_bytes = (uint64_t)L * N * ldh * 2, new_bytes = (uint64_t)U * t->new16_unit;
+  const uint64_t cache_bytes = (uint64_t)L * N * row_bytes, new_bytes = (uint64_t)U * t->new16_unit;
   if (alias_new16) {
     // one area for both: the layer cache during the forward, the dH rows afterwards
     t->rcache16 = rtake(cache_bytes > new_bytes ? cache_bytes : new_bytes);
@@ -459,6 +465,13 @@ __device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
 __device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, const Unit& u, int l) {
   return (__nv_bfloat16*)((unsigned char*)u.d16 + c.a->lay.new16_off[l]);
 }
+// split mode: the same caches with FP32 rows of stride ldy
+__device__ __forceinline__ float* cache32w(const TcCtx& c, int l) {
+  return (float*)(c.region + c.a->lay.rcache16) + (size_t)l * c.N * c.ldy;
+}
+__device__ __forceinline__ float* new32(const TcCtx& c, const Unit& u, int l) {
+  return (float*)((unsigned char*)u.d16 + c.a->lay.new16_off[l]);
+}
 
 // acc2[0..4) (pairs of float32) += w * bf16 row chunk at p (16 bytes), f32x2 arithmetic
 __device__ __forceinline__ void fma_chunk2(uint64_t* acc2, uint64_t w2, const __nv_bfloat16* p) {
@@ -482,8 +495,58 @@ __device__ __forceinline__ void fma_chunk(float* acc, float w, const __nv_bfloat
   acc[7] += w * bf16hi(u.w);
 }
 
+// 8 FP32 values as hi = bf16(x) and lo = bf16(x - hi), packed two per 32-bit word.
+__device__ __forceinline__ void split_hi_lo(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
+    h[p] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[p] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// one element as hi and lo BF16
+__device__ __forceinline__ void split1(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// acc[0..8) += w * FP32 row chunk at p (two 16-byte loads)
+__device__ __forceinline__ void fma_chunk32(float* acc, float w, const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  acc[0] = fmaf(w, a.x, acc[0]);
+  acc[1] = fmaf(w, a.y, acc[1]);
+  acc[2] = fmaf(w, a.z, acc[2]);
+  acc[3] = fmaf(w, a.w, acc[3]);
+  acc[4] = fmaf(w, b.x, acc[4]);
+  acc[5] = fmaf(w, b.y, acc[5]);
+  acc[6] = fmaf(w, b.z, acc[6]);
+  acc[7] = fmaf(w, b.w, acc[7]);
+}
+
+// tanh(x) - x for |x| < 0.5: x^3 times the Taylor series of tanh from its x^3 term on
+// (coefficients 2^2n (2^2n - 1) B_2n / (2n)!, B_2n the Bernoulli numbers), through x^15;
+// the truncation is below 1e-7 of tanh(x) at |x| = 0.5.
+__device__ __forceinline__ float tanh_minus_x(float x) {
+  const float x2 = x * x;
+  float p = -929569.f / 638512875.f;
+  p = fmaf(p, x2, 21844.f / 6081075.f);
+  p = fmaf(p, x2, -1382.f / 155925.f);
+  p = fmaf(p, x2, 62.f / 2835.f);
+  p = fmaf(p, x2, -17.f / 315.f);
+  p = fmaf(p, x2, 2.f / 15.f);
+  p = fmaf(p, x2, -1.f / 3.f);
+  return p * x2 * x;
+}
+
 // Issue the MMAs of nt tiles (unit thread 0), commit, and wait (bounded).  Returns false on
-// timeout (uniform across the unit).
+// timeout (uniform across the unit).  S: each tile's lo part (at lo_off) is multiplied into
+// the same accumulator after its hi part.
+template <bool S>
 __device__ bool run_mmas(const TcCtx& c, Unit& u, int nt) {
   fence_proxy_async();
   unit_sync(u);
@@ -498,6 +561,14 @@ __device__ bool run_mmas(const TcCtx& c, Unit& u, int nt) {
         const uint64_t ad = sdesc(a0 + t * 128 * 4 * F + kb * 256, 128, sbo);
         const uint64_t bd = sdesc(b0 + kb * 256, 128, sbo);
         mma_bf16(u.tbase + t * F, ad, bd, idesc, kb > 0 ? 1u : 0u);
+      }
+      if (S) {
+        const uint32_t alo = a0 + c.a->lay.lo_off;
+        for (int kb = 0; kb < (2 * F) / 16; ++kb) {
+          const uint64_t ad = sdesc(alo + t * 128 * 4 * F + kb * 256, 128, sbo);
+          const uint64_t bd = sdesc(b0 + kb * 256, 128, sbo);
+          mma_bf16(u.tbase + t * F, ad, bd, idesc, 1u);
+        }
       }
     }
     mma_commit(u.bar);
@@ -516,11 +587,14 @@ __device__ bool run_mmas(const TcCtx& c, Unit& u, int nt) {
 // Forward epilogue for rows [r0, r0 + R) of layer l: Y = acc + b.  l < L: H^l = tanh(Y)
 // stored BF16 (and Y in FP32 when the call needs the incremental step).  l == L: Y^L in
 // FP32, or, for the forward-only call, H^L = tanh(Y^L) in FP32 for the readout.
+// S: H^l (l < L) stored in FP32 with an accurate tanh.
+template <bool S>
 __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r0, int l, bool keep_y) {
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, ldh = c.ldh, ldy = c.ldy;
-  __nv_bfloat16* h16 = l < L ? cache16w(c, l) + (size_t)r0 * ldh : nullptr;
+  __nv_bfloat16* h16 = l < L && !S ? cache16w(c, l) + (size_t)r0 * ldh : nullptr;
+  float* h32 = l < L && S ? cache32w(c, l) + (size_t)r0 * ldy : nullptr;
   float* y32 = cacheY(c, l) + (size_t)r0 * ldy;
   for (int t = 0; t < nt; ++t) {
     const int q = t * 128 + q4 * 32 + lane;
@@ -537,12 +611,18 @@ __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r
             yo[0] = make_float4(sexp(v[0]), sexp(v[1]), sexp(v[2]), sexp(v[3]));
             yo[1] = make_float4(sexp(v[4]), sexp(v[5]), sexp(v[6]), sexp(v[7]));
           }
-          uint4 w;
-          w.x = pack_bf16(tanh_fast(v[0]), tanh_fast(v[1]));
-          w.y = pack_bf16(tanh_fast(v[2]), tanh_fast(v[3]));
-          w.z = pack_bf16(tanh_fast(v[4]), tanh_fast(v[5]));
-          w.w = pack_bf16(tanh_fast(v[6]), tanh_fast(v[7]));
-          *reinterpret_cast<uint4*>(h16 + (size_t)q * ldh + col) = w;
+          if (S) {
+            float4* ho = reinterpret_cast<float4*>(h32 + (size_t)q * ldy + col);
+            ho[0] = make_float4(tanhf(v[0]), tanhf(v[1]), tanhf(v[2]), tanhf(v[3]));
+            ho[1] = make_float4(tanhf(v[4]), tanhf(v[5]), tanhf(v[6]), tanhf(v[7]));
+          } else {
+            uint4 w;
+            w.x = pack_bf16(tanh_fast(v[0]), tanh_fast(v[1]));
+            w.y = pack_bf16(tanh_fast(v[2]), tanh_fast(v[3]));
+            w.z = pack_bf16(tanh_fast(v[4]), tanh_fast(v[5]));
+            w.w = pack_bf16(tanh_fast(v[6]), tanh_fast(v[7]));
+            *reinterpret_cast<uint4*>(h16 + (size_t)q * ldh + col) = w;
+          }
         } else if (keep_y) {
           yo[0] = make_float4(sexp(v[0]), sexp(v[1]), sexp(v[2]), sexp(v[3]));
           yo[1] = make_float4(sexp(v[4]), sexp(v[5]), sexp(v[6]), sexp(v[7]));
@@ -557,13 +637,21 @@ __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r
   unit_sync(u);
 }
 
-// Forward of the configuration in c.spin (unit = whole CTA): fills the cache.
+// Forward of the configuration in c.spin (unit = whole CTA): fills the cache.  S: the layer
+// cache in FP32 and X = [A_hat H ; H] as hi + lo tiles.
+template <bool S>
 __device__ bool tc_forward(const TcCtx& c, Unit& u) {
-  const int N = c.N, F = c.F, L = c.L, ldh = c.ldh;
+  const int N = c.N, F = c.F, L = c.L, ldh = c.ldh, ldy = c.ldy;
   const DevGraph& g = c.a->g;
-  __nv_bfloat16* c0 = cache16w(c, 0);
-  for (int i = u.tid; i < N * F; i += u.nthr)
-    c0[(size_t)(i / F) * ldh + i % F] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
+  if (S) {
+    float* c0 = cache32w(c, 0);
+    for (int i = u.tid; i < N * F; i += u.nthr)
+      c0[(size_t)(i / F) * ldy + i % F] = c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F];
+  } else {
+    __nv_bfloat16* c0 = cache16w(c, 0);
+    for (int i = u.tid; i < N * F; i += u.nthr)
+      c0[(size_t)(i / F) * ldh + i % F] = __float2bfloat16_rn(c.emb[(c.spin[i / F] > 0 ? 0 : 1) * F + i % F]);
+  }
   unit_sync(u);
   const int F8 = F / 8;
   const int rows_per_pass = c.T * 128;
@@ -577,6 +665,19 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
         const int q = idx / F8, ch = idx - q * F8, v = r0 + q;
         const int k0 = c.rp[v], k1 = c.rp[v + 1];
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (S) {
+          const float* hp32 = cache32w(c, l - 1);
+          for (int k = k0; k < k1; ++k) fma_chunk32(acc, c.wfs[k], hp32 + (size_t)__ldg(g.col + k) * ldy + ch * 8);
+          const unsigned lo = c.a->lay.lo_off;
+          uint4 hi, lw;
+          split_hi_lo(acc, hi, lw);
+          *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch)) = hi;
+          *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, ch) + lo) = lw;
+          split_hi_lo(hp32 + (size_t)v * ldy + ch * 8, hi, lw);
+          *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) = hi;
+          *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch) + lo) = lw;
+          continue;
+        }
         for (int k = k0; k < k1; ++k) fma_chunk(acc, c.wfs[k], hp + (size_t)__ldg(g.col + k) * ldh + ch * 8);
         uint4 w;
         w.x = pack_bf16(acc[0], acc[1]);
@@ -587,8 +688,8 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
         *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
             *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
       }
-      if (!run_mmas(c, u, nt)) return false;
-      epilogue_fwd(c, u, nt, R, r0, l, c.a->op != TC_FWD);
+      if (!run_mmas<S>(c, u, nt)) return false;
+      epilogue_fwd<S>(c, u, nt, R, r0, l, c.a->op != TC_FWD);
     }
   }
   return true;
@@ -644,7 +745,9 @@ __device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
 // dX rows of a bond group at layer l, gathered into the unit's A tiles:
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
 // One thread per (row, 8-feature chunk): the chunk of the message and the chunk of the self
-// term, so that every thread of the unit does the same amount of work.
+// term, so that every thread of the unit does the same amount of work.  S: dH rows in FP32,
+// the gathered rows stored as hi + lo tiles.
+template <bool S>
 __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q0, int n) {
   const int F = c.F, G = c.G, ldh = c.ldh;
   const int F8 = F / 8;
@@ -663,6 +766,36 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
     const int v = rec & 0xFFFF;
     const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
     const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
+    if (S) {
+      const float* drow32 = new32(c, u, l - 1) + (size_t)offp[k] * c.ldy + ch * 8;
+      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = 0; t < dg; ++t) {
+        const int p0 = np[t];
+        if (p0 < sprev) fma_chunk32(acc, c.wfs[k0 + t], drow32 + (size_t)p0 * c.ldy);
+      }
+      const unsigned lo = c.a->lay.lo_off;
+      uint4 hi, lw;
+      split_hi_lo(acc, hi, lw);
+      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch)) = hi;
+      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch) + lo) = lw;
+      float self[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (r < sprev) {
+        const float4 a0 = *reinterpret_cast<const float4*>(drow32 + (size_t)r * c.ldy);
+        const float4 a1 = *reinterpret_cast<const float4*>(drow32 + (size_t)r * c.ldy + 4);
+        self[0] = a0.x;
+        self[1] = a0.y;
+        self[2] = a0.z;
+        self[3] = a0.w;
+        self[4] = a1.x;
+        self[5] = a1.y;
+        self[6] = a1.z;
+        self[7] = a1.w;
+      }
+      split_hi_lo(self, hi, lw);
+      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch)) = hi;
+      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch) + lo) = lw;
+      continue;
+    }
     uint64_t acc2[4] = {0, 0, 0, 0};  // pairs of float32 zeros
     // neighbours outside ball_{l-1} have dH = 0: they take weight 0 on a valid row (row 0 of
     // the bond), so the loop has no branch and keeps two loads in flight; adding the zero
@@ -702,6 +835,12 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
 // dH = tanh(Y + dY) - tanh(Y) of 8 units from se = copysign(exp(-2|Y|), Y) and dY:
 // with e = exp(-2|Y|), H = sgn(Y)(1-e)/(1+e) and 1 - H^2 = 4e/(1+e)^2, so
 // dH = t (1 - H^2)/(1 + H t) = 4 e t / ((1 + e)((1 + e) + sgn(Y)(1 - e) t)), t = tanh(dY).
+// S: t to FP32 accuracy (odd Taylor series) instead of the approximate hardware tanh.
+template <bool S>
+__device__ __forceinline__ float tanh_small(float x) {
+  return S ? x + tanh_minus_x(x) : tanh_fast(x);
+}
+template <bool S>
 __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, float* d) {
   // common case for all 8 units without branches (|dY| < 0.5 and no swing across
   // saturation); if any unit needs more, all 8 are redone by the full rule below, which gives
@@ -710,8 +849,8 @@ __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, fl
 #pragma unroll
   for (int i = 0; i < 8; i += 2) {
     float den0, den1;
-    delta_tanh_pair(fabsf(se[i]), fabsf(se[i + 1]), se[i], se[i + 1], tanh_fast(dy[i]), tanh_fast(dy[i + 1]), d[i],
-                    d[i + 1], den0, den1);
+    delta_tanh_pair(fabsf(se[i]), fabsf(se[i + 1]), se[i], se[i + 1], tanh_small<S>(dy[i]), tanh_small<S>(dy[i + 1]),
+                    d[i], d[i + 1], den0, den1);
     slow |= !(fabsf(dy[i]) < 0.5f) | !(den0 > 1e-3f) | !(fabsf(dy[i + 1]) < 0.5f) | !(den1 > 1e-3f);
   }
   if (!slow) return;
@@ -719,7 +858,7 @@ __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, fl
   for (int i = 0; i < 8; ++i) {
     const float e = fabsf(se[i]);
     const float sg = se[i] < 0.f ? -1.f : 1.f;
-    const float tt = fabsf(dy[i]) < 0.5f ? tanh_fast(dy[i]) : tanhf(dy[i]);
+    const float tt = fabsf(dy[i]) < 0.5f ? tanh_small<S>(dy[i]) : tanhf(dy[i]);
     const float ope = 1.f + e;
     const float den = ope * (ope + sg * (1.f - e) * tt);
     if (den > 1e-3f) {
@@ -736,13 +875,15 @@ __device__ __forceinline__ void delta_tanh8(const float* se, const float* dy, fl
 // dY in TMEM -> dH = t (1 - H^2) / (1 + H t), t = tanh(dY), for group rows [0, R) at layer
 // l.  l < L: dH stored (BF16) as the next layer's input.  l == L: each thread reduces its
 // columns of dH . w_r into per-row partials (Re, Im) for the Delta reduction.
+template <bool S>
 __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int nb, int q0) {
   const int warp = u.tid >> 5, lane = u.tid & 31;
   const int q4 = warp & 3, wg = warp >> 2;
   const int F = c.F, L = c.L, G = c.G, ldh = c.ldh, ldy = c.ldy;
   const int* offl = u.soff + l * (G + 1);
   const int R = offl[nb];
-  __nv_bfloat16* dout = l < L ? new16(c, u, l) : nullptr;
+  __nv_bfloat16* dout = l < L && !S ? new16(c, u, l) : nullptr;
+  float* dout32 = l < L && S ? new32(c, u, l) : nullptr;
   const float* Yl = cacheY(c, l);
   const int* offL = u.soff + L * (G + 1);
   for (int t = 0; t < nt; ++t) {
@@ -772,8 +913,12 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
           const float4 a1 = *reinterpret_cast<const float4*>(Yl + (size_t)v * ldy + col + 4);
           const float se[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           float d[8];
-          delta_tanh8(se, dy[h2], d);
-          if (l < L) {
+          delta_tanh8<S>(se, dy[h2], d);
+          if (S && l < L) {
+            float4* o = reinterpret_cast<float4*>(dout32 + (size_t)q * ldy + col);
+            o[0] = make_float4(d[0], d[1], d[2], d[3]);
+            o[1] = make_float4(d[4], d[5], d[6], d[7]);
+          } else if (l < L) {
             uint4 w;
             w.x = pack_bf16(d[0], d[1]);
             w.y = pack_bf16(d[2], d[3]);
@@ -800,6 +945,7 @@ __device__ void epilogue_delta(const TcCtx& c, const Unit& u, int l, int nt, int
 }
 
 // Incremental Delta log Psi of the unit's bonds slot_e[0..nb): results in res[2k], res[2k+1].
+template <bool S>
 __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, L = c.L, G = c.G;
@@ -811,7 +957,10 @@ __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
     const int e = u.slot_e[k];
     const int self = __ldg(g.edges + 2 * e + r), other = __ldg(g.edges + 2 * e + (1 - r));
     const float dv = c.emb[(c.spin[other] > 0 ? 0 : 1) * F + f] - c.emb[(c.spin[self] > 0 ? 0 : 1) * F + f];
-    d0[(size_t)(u.soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
+    if (S)
+      new32(c, u, 0)[(size_t)(u.soff[k] + r) * c.ldy + f] = dv;
+    else
+      d0[(size_t)(u.soff[k] + r) * c.ldh + f] = __float2bfloat16_rn(dv);
   }
   unit_sync(u);
   // each layer in passes of at most T tiles of 128 rows
@@ -819,10 +968,10 @@ __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
     const int R = u.soff[l * (G + 1) + nb];
     for (int q0 = 0; q0 < R; q0 += c.T * 128) {
       const int n = min(c.T * 128, R - q0);
-      gather_delta(c, u, l, nb, q0, n);
+      gather_delta<S>(c, u, l, nb, q0, n);
       const int nt = (n + 127) / 128;
-      if (!run_mmas(c, u, nt)) return false;
-      epilogue_delta(c, u, l, nt, nb, q0);
+      if (!run_mmas<S>(c, u, nt)) return false;
+      epilogue_delta<S>(c, u, l, nt, nb, q0);
     }
   }
   // Delta_k = sum over the bond's last-layer rows of the per-row partials (one warp per bond)
@@ -848,6 +997,8 @@ __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
   return true;
 }
 
+// S: split operands (hi + lo BF16 on the tensor cores, FP32 feature rows, accurate tanh).
+template <bool S>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_fail;
@@ -943,7 +1094,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     __syncthreads();
     // unit 0 and the whole CTA share mbarrier 0: its waiter (thread 0) carries the phase
     if (threadIdx.x == 0) whole.phase = u.phase;
-    ok = tc_forward(c, whole);
+    ok = tc_forward<S>(c, whole);
     if (threadIdx.x == 0) u.phase = whole.phase;
     if (!ok) break;
     if (a.op == TC_FWD) {
@@ -992,7 +1143,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       const int nb = min(c.G, b_hi - t0);
       if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
       unit_sync(u);
-      if (!tc_group(c, u, nb)) break;
+      if (!tc_group<S>(c, u, nb)) break;
       // each bond's term Jxy/2 exp(Delta) by its own lane (in place of its Delta), then
       // thread 0 adds them in bond order
       if (u.tid < nb) {
@@ -1131,7 +1282,7 @@ __device__ bool tcm_forward(const TcCtx& c, Unit& u, const TcmArgs& a, float* Ys
         *reinterpret_cast<uint4*>(a_row_chunk(u, F, q, F8 + ch)) =
             *reinterpret_cast<const uint4*>(hp + (size_t)v * ldh + ch * 8);
       }
-      if (!run_mmas(c, u, nt)) return false;
+      if (!run_mmas<false>(c, u, nt)) return false;
       for (int t = 0; t < nt; ++t) {
         const int q = t * 128 + q4 * 32 + lane;
         for (int ch = wg; ch < F8; ch += u.nwg) {
@@ -1282,9 +1433,9 @@ __device__ bool tcm_group(const TcCtx& c, Unit& u, const TcmArgs& a, const TcmSl
     const int R = u.soff[l * (G + 1) + nb];
     for (int q0 = 0; q0 < R; q0 += c.T * 128) {
       const int n = min(c.T * 128, R - q0);
-      gather_delta(c, u, l, nb, q0, n);
+      gather_delta<false>(c, u, l, nb, q0, n);
       const int nt = (n + 127) / 128;
-      if (!run_mmas(c, u, nt)) return false;
+      if (!run_mmas<false>(c, u, nt)) return false;
       tcm_epilogue(c, u, a, S, ug, l, nt, nb, q0);
     }
   }
@@ -1716,39 +1867,6 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint32_t a_addr, uint
              (accumulate || kb > 0) ? 1u : 0u);
 }
 
-// 8 FP32 values as hi = bf16(x) and lo = bf16(x - hi), packed two per 32-bit word.
-__device__ __forceinline__ void split_hi_lo(const float* x, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
-    const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
-    h[p] = *reinterpret_cast<const uint32_t*>(&hb);
-    l[p] = *reinterpret_cast<const uint32_t*>(&lb);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-// one element as hi and lo BF16
-__device__ __forceinline__ void split1(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(x);
-  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
-// acc[0..8) += w * FP32 row chunk at p (two 16-byte loads)
-__device__ __forceinline__ void fma_chunk32(float* acc, float w, const float* p) {
-  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-  acc[0] = fmaf(w, a.x, acc[0]);
-  acc[1] = fmaf(w, a.y, acc[1]);
-  acc[2] = fmaf(w, a.z, acc[2]);
-  acc[3] = fmaf(w, a.w, acc[3]);
-  acc[4] = fmaf(w, b.x, acc[4]);
-  acc[5] = fmaf(w, b.y, acc[5]);
-  acc[6] = fmaf(w, b.z, acc[6]);
-  acc[7] = fmaf(w, b.w, acc[7]);
-}
-
 // small-parameter accumulators: [W_e (2F), b_e (F)] [b (F)] [w_r (2F+4)] [b_r (2)]
 __device__ __forceinline__ int sp_We(int F) { return 0; }
 __device__ __forceinline__ int sp_b(int F) { return 3 * F; }
@@ -2175,7 +2293,7 @@ struct TcPlan {
   size_t ws_bytes = 0;
 };
 
-static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, TcPlan* p, int* maxball) {
+static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, TcPlan* p, int* maxball, int split) {
   if (m.F % 16 != 0 || m.F > 64 || m.L < 1 || !m.shared || !g->pack_ok) return GNA_ERR_UNSUPPORTED;
   DeviceInfo di;
   gna_status st = device_info(&di);
@@ -2184,7 +2302,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   for (int l = 0; l <= kMaxL; ++l) maxball[l] = (l <= m.L && l <= g->d.Lmax) ? g->max_ball[l] : 0;
   const int maxspan = g->max_span[m.L];
   const int T = tc_tiles_per_unit(m.F);
-  if (tc_units(m.F) * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
+  if (tc_units(m.F, split) * T * m.F > kTmemCols) return GNA_ERR_UNSUPPORTED;
   const size_t budget = (size_t)di.smem_optin - 2048;
   // bonds per group: as many as fill the T tiles at the last layer in one pass; a layer with
   // more rows runs in several passes
@@ -2197,7 +2315,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   // the group size with the fewest passes per bond (ties: the larger) among those that fit
   int g_fit = 0, best = 1 << 30;
   for (int gg = op == TC_ELOC ? 16 : 1; gg >= 1; --gg) {
-    tc_layout(m, maxball, maxspan, gg, 1, op == TC_ELOC, &lay);
+    tc_layout(m, maxball, maxspan, gg, 1, op == TC_ELOC, &lay, split);
     if (lay.smem_total > budget) continue;
     const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
     if (cost < best) {
@@ -2207,14 +2325,14 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   }
   if (g_fit > 0) {
     p->region_in_smem = 1;
-    tc_layout(m, maxball, maxspan, g_fit, 1, op == TC_ELOC, &lay);
+    tc_layout(m, maxball, maxspan, g_fit, 1, op == TC_ELOC, &lay, split);
   } else {
     // region in the workspace: the group size by the same cost model among those that fit,
     // up to 8 bonds (larger groups spill the per-CTA regions out of L2: triangular 144,
     // F = 48: 8 bonds 36.8 ms, 16 bonds 42.6 ms per 4096 configurations)
     int Gg = 0;
     for (int gg = op == TC_ELOC ? 8 : 1; gg >= 1; --gg) {
-      tc_layout(m, maxball, maxspan, gg, 0, op == TC_ELOC, &lay);
+      tc_layout(m, maxball, maxspan, gg, 0, op == TC_ELOC, &lay, split);
       if (lay.smem_total > budget) continue;
       const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
       if (cost < best) {
@@ -2223,7 +2341,7 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
       }
     }
     if (Gg < 1) return GNA_ERR_UNSUPPORTED;
-    tc_layout(m, maxball, maxspan, Gg, 0, op == TC_ELOC, &lay);
+    tc_layout(m, maxball, maxspan, Gg, 0, op == TC_ELOC, &lay, split);
     p->region_in_smem = 0;
   }
   // At most 512 / kTmemCols CTAs may hold TMEM on one SM at a time: request enough shared
@@ -2231,9 +2349,10 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   const uint32_t min_smem = (uint32_t)(228u * 1024u / (512 / kTmemCols + 1)) + 1024u;
   if (lay.smem_total < min_smem) lay.smem_total = min_smem;
   p->lay = lay;
-  GNA_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_total));
+  const void* kfn = split ? (const void*)k_tc<true> : (const void*)k_tc<false>;
+  GNA_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_total));
   int occ = 0;
-  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_tc, kTcThreads, lay.smem_total));
+  GNA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kTcThreads, lay.smem_total));
   if (occ < 1) occ = 1;
   if (occ * kTmemCols > 512) return GNA_ERR_UNSUPPORTED;
   int64_t grid = (int64_t)di.sms * occ;
@@ -2244,14 +2363,14 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   return GNA_OK;
 }
 
-gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes) {
+gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes, int split) {
   if (B == 0) {
     *bytes = 0;
     return GNA_OK;
   }
   TcPlan p;
   int maxball[kMaxL + 1];
-  gna_status st = tc_plan(g, m, op, B, &p, maxball);
+  gna_status st = tc_plan(g, m, op, B, &p, maxball, split);
   if (st != GNA_OK) return st;
   *bytes = p.ws_bytes;
   return GNA_OK;
@@ -2261,7 +2380,7 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   if (call.B == 0) return GNA_OK;
   TcPlan p;
   TcArgs a;
-  gna_status st = tc_plan(call.g, call.m, call.op, call.B, &p, a.maxball);
+  gna_status st = tc_plan(call.g, call.m, call.op, call.B, &p, a.maxball, call.split);
   if (st != GNA_OK) return st;
   if (ws_bytes < p.ws_bytes || (p.ws_bytes > 0 && !ws)) return GNA_ERR_WORKSPACE;
   a.g = call.g->d;
@@ -2276,7 +2395,10 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   a.dlogpsi = call.dlogpsi;
   a.gregion = (unsigned char*)ws;
   a.region_in_smem = p.region_in_smem;
-  k_tc<<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
+  if (call.split)
+    k_tc<true><<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
+  else
+    k_tc<false><<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
 }

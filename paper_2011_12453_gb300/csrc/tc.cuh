@@ -17,6 +17,7 @@ struct TcCall {
   double* logpsi;  // TC_FWD: [B][2]
   double* eloc;    // TC_ELOC: [B][2]
   float* dlogpsi;  // TC_ELOC: [B][E] or NULL
+  int split = 0;   // 1: operands as hi + lo BF16 pairs (GNA_PREC_BF16X2)
 };
 
 // Plain-move Metropolis sweeps of BF16 models on the tensor cores (same move rule and
@@ -46,7 +47,7 @@ struct TcbCall {
   double* grad;       // [P]
 };
 
-gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes);
+gna_status tc_workspace(const gna_graph* g, const Dims& m, int op, int64_t B, size_t* bytes, int split);
 gna_status tcb_workspace(const gna_graph* g, const Dims& m, int64_t B, size_t* bytes);
 gna_status tcb_run(const TcbCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 // Same backward with its scratch in a fixed array of scratch_bytes (the grid is reduced to fit).

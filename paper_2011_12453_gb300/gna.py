@@ -24,7 +24,7 @@ GNA_ERR_WORKSPACE = -5
 GNA_ERR_UNSUPPORTED = -6
 GNA_WARN_DEGENERATE_WEIGHTS = 1
 
-PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
 ACT_TANH, ACT_RELU_LN = 0, 1
 ELOC_FULL, ELOC_INCREMENTAL = 0, 1
 OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIGHTS, OP_ISGO_GRAD, \

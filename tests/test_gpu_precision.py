@@ -24,6 +24,7 @@ from paper_2011_12453_gb300 import build as B, gna, workloads as W
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {(gna.PREC_BF16, 0.1): (1e-4, 5e-2, 0.6), (gna.PREC_BF16, 0.3): (5e-3, 2e-2, 5e-2),
+          (gna.PREC_BF16X2, 0.1): (1e-4, 1e-3, 1e-3), (gna.PREC_BF16X2, 0.3): (1e-4, 1e-3, 1e-3),
           (gna.PREC_FP32, 0.1): (1e-6, 1e-4, 1e-3), (gna.PREC_FP32, 0.3): (1e-6, 1e-4, 1e-3)}
 
 
@@ -37,7 +38,7 @@ def torch():
 
 
 @pytest.mark.parametrize("scale", [0.1, 0.3])
-@pytest.mark.parametrize("prec", [gna.PREC_BF16, gna.PREC_FP32])
+@pytest.mark.parametrize("prec", [gna.PREC_BF16, gna.PREC_BF16X2, gna.PREC_FP32])
 def test_energy_variance_gradient_errors(torch, prec, scale):
     g = W.kagome(6)
     F, L, Bn = 32, 4, 48
@@ -45,7 +46,7 @@ def test_energy_variance_gradient_errors(torch, prec, scale):
     model = gna.Model(F, L, prec)
     theta = torch.tensor(W.random_theta(F, L, seed=0, scale=scale), dtype=torch.float32, device="cuda")
     th = theta.double().cpu().numpy()
-    if prec == gna.PREC_BF16:
+    if prec in (gna.PREC_BF16, gna.PREC_BF16X2):
         o = 3 * F
         th[o:o + 2 * F * F] = torch.tensor(th[o:o + 2 * F * F], dtype=torch.float32).to(torch.bfloat16).double().numpy()
     Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
@@ -71,7 +72,7 @@ def test_energy_variance_gradient_errors(torch, prec, scale):
     from_O = gna.backward(graph, model, theta, s, cot_o).cpu().numpy()
     err_gE = np.abs(from_E - g_o).max() / gmax
     err_gO = np.abs(from_O - g_o).max() / gmax
-    name = "BF16" if prec == gna.PREC_BF16 else "FP32"
+    name = {gna.PREC_BF16: "BF16", gna.PREC_BF16X2: "BF16X2", gna.PREC_FP32: "FP32"}[prec]
     print(f"\n{name} scale {scale}: E {Ebar.real:.5f} (sigma_E {np.sqrt(var):.2e}) rel err {err_E:.2e}; sigma^2 rel err "
           f"{err_var:.2e}; gradient err / max {err_g:.2e} (from E_loc {err_gE:.2e}, from d log Psi {err_gO:.2e})")
     bE, bV, bG = BOUNDS[(prec, scale)]

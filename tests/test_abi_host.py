@@ -44,7 +44,7 @@ def test_num_params_matches_layout(F, L, shared):
 
 
 @pytest.mark.parametrize("args", [(0, 2, 0, 0, 1), (65, 2, 0, 0, 1), (16, 9, 0, 0, 1), (16, 2, 2, 0, 1),
-                                  (16, 2, 0, 3, 1), (16, 2, 0, 0, 2), (24, 2, 0, 2, 1)])
+                                  (16, 2, 0, 4, 1), (16, 2, 0, 0, 2), (24, 2, 0, 2, 1), (24, 2, 0, 3, 1)])
 def test_model_desc_rejects(args):
     d = gna.ModelDesc()
     assert gna.lib().gna_model_desc_init(ctypes.byref(d), *args) == gna.GNA_ERR_INVALID_ARG
@@ -52,7 +52,7 @@ def test_model_desc_rejects(args):
 
 def test_model_desc_accepts_relu_ln():
     d = gna.ModelDesc()
-    for prec in (0, 1, 2):
+    for prec in (0, 1, 2, 3):
         assert gna.lib().gna_model_desc_init(ctypes.byref(d), 16, 3, gna.ACT_RELU_LN, prec, 1) == gna.GNA_OK
         assert d.act == gna.ACT_RELU_LN
 

@@ -64,13 +64,21 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default=os.environ.get("GNA_BENCH_PREC", "auto"))
+    p.add_argument("--prec", default=os.environ.get("GNA_BENCH_PREC", "auto"),
+                   help="bf16x2 (default: split-operand tensor-core GEMMs, the path that meets the energy, "
+                        "variance and gradient accuracy targets), bf16 or fp32")
     p.add_argument("--backward-prec", default="same", choices=["same", "fp32"],
                    help="arithmetic of the step's backward: that of --prec (default) or FP32, whose ISGO "
                         "gradient stays accurate at nearly flat wavefunctions")
     p.add_argument("--workload", default="kagome108", choices=sorted(WORKLOADS))
     p.add_argument("--chains", type=int, default=None, help="override the workload's chain count")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--extra", default="triangular144,kagome432",
+                   help="comma-separated workloads also timed after the headline one (ISGO step, local-energy "
+                        "samples/s, roofline, energy agreement), or 'none'")
+    p.add_argument("--extra-reuse", type=int, default=2,
+                   help="reuse updates timed for the Kagome 432 workload (its 10-update iteration is reported "
+                        "as the timed sweeps + 10 x the mean timed update)")
     p.add_argument("--only", default=None, choices=["eloc", "eloc_full", "metropolis", "backward", "forward"],
                    help="time one call of the path alone (for profiling); prints a short JSON line")
     a = p.parse_args()
@@ -337,6 +345,105 @@ def sweep_flops(g, F, L, ball, deg_of, spins_np, steps_per_chain):
     per_step = (anti * per_bond[None, :]).sum(axis=1) / g.n_edges
     return float((fwd + steps_per_chain * per_step).sum())
 
+PRECS = {"bf16": 2, "bf16x2": 3, "fp32": 1}
+
+
+def measure_workload(key, prec_name, dev, flush, K_timed, peaks, peak_kind):
+    """One ISGO iteration of another workload, timed with CUDA events on the current stream:
+    the recorded sweeps of all chains (plain moves on the tensor-core sampler), then
+    min(K, K_timed) reuse updates over all S x C samples (forward, incremental local energy,
+    ISGO weights, backward + SGD; L2 flushed before each).  Reports the mean update (the ISGO
+    step), the iteration (sweeps + K updates; extrapolated from the timed updates when
+    K_timed < K), local-energy samples/s with the roofline of k_tc, and the energy agreement
+    with the plain FP32 full re-evaluation on a subset of the samples."""
+    import torch
+
+    from paper_2011_12453_gb300 import gna
+
+    wl = dict(WORKLOADS[key])
+    g = make_graph(wl)
+    F, L, C = wl["F"], wl["L"], wl["chains"]
+    S, K = wl["recorded_sweeps"], wl["reuse"]
+    N = g.n_sites
+    Bn = S * C
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, PRECS[prec_name])
+    model32 = gna.Model(F, L, gna.PREC_FP32)
+    theta = torch.tensor(W.random_theta(F, L, wl["theta_seed"]), dtype=torch.float32, device=dev)
+    chains = torch.tensor(W.random_spins(N, C, wl["spin_seed"]), device=dev)
+    lp0 = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
+    lp = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
+    E = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
+    grad = torch.empty(model.num_params, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # warm-up (untimed): one sweep of every chain, one update on a slice with a copy of theta
+    gna.metropolis_sweep(graph, model, theta, chains, 1, 0, 777, 0)
+    sl = chains[:min(C, 1024)].contiguous()
+    th_w = theta.clone()
+    l_w = gna.forward(graph, model, th_w, sl)
+    E_w = gna.local_energy(graph, model, th_w, sl, gna.ELOC_INCREMENTAL)
+    c_w, _ = gna.isgo_weights(l_w, l_w, E_w)
+    gna.sgd_update(model, th_w, gna.backward(graph, model, th_w, sl, c_w), 1e-3)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    samples, _, _, _ = gna.metropolis_sweep(graph, model, theta, chains, S, 1, 12345, N, record_logpsi=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_sweeps = e0.elapsed_time(e1)
+    s = samples.view(Bn, N)
+    kt = min(K, K_timed)
+    ph = np.zeros((kt, 4))
+    for k in range(kt):
+        flush.zero_()
+        ms = [ev() for _ in range(5)]
+        cur = lp0 if k == 0 else lp
+        ms[0].record(stream)
+        gna.forward(graph, model, theta, s, out=cur)
+        ms[1].record(stream)
+        gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
+        ms[2].record(stream)
+        cot, stats = gna.isgo_weights(cur, lp0, E)
+        ms[3].record(stream)
+        gna.backward(graph, model, theta, s, cot, out=grad)
+        gna.sgd_update(model, theta, grad, 1e-4)
+        ms[4].record(stream)
+        torch.cuda.synchronize()
+        ph[k] = [ms[i].elapsed_time(ms[i + 1]) for i in range(4)]
+    upd = float(ph.sum(axis=1).mean())
+    t_eloc = float(ph[:, 1].mean())
+    spins_np = s.cpu().numpy()
+    deg = np.bincount(g.edges.ravel(), minlength=N)
+    ball = gna.ball_sizes_host(N, g.edges, L)
+    fl = float(incremental_flops(g, F, L, ball, deg, spins_np).sum())
+    achieved = fl / (t_eloc / 1000.0) / 1e12
+    nc = min(Bn, wl["comparator_samples"])
+    sub = s[:nc].contiguous()
+    E_ours = E[:nc].cpu().numpy()
+    E_full = gna.local_energy(graph, model32, theta, sub, gna.ELOC_FULL).cpu().numpy()
+    rel = abs(E_ours[:, 0].mean() - E_full[:, 0].mean()) / abs(E_full[:, 0].mean())
+    per_sample = np.abs(E_ours[:, 0] - E_full[:, 0]) / np.abs(E_full[:, 0]).clip(1e-12)
+    return {"workload": wl["workload"], "dtype": prec_name, "n_sites": N, "L": L, "F": F, "chains": C,
+            "recorded_sweeps": S, "samples": Bn, "reuse": K, "reuse_timed": kt, "proposal": "plain",
+            "sweeps_ms": t_sweeps, "isgo_step_ms": upd,
+            "isgo_iteration_ms": t_sweeps + K * upd, "isgo_iteration_extrapolated": kt < K,
+            "phases_ms_per_update": {"forward": float(ph[:, 0].mean()), "local_energy": t_eloc,
+                                     "isgo_weights": float(ph[:, 2].mean()), "backward_sgd": float(ph[:, 3].mean())},
+            "eloc_samples_per_s": Bn / (t_eloc / 1000.0),
+            "sample_updates_per_s": Bn / (upd / 1000.0),
+            "roofline": {"bound": "tensor", "kernel": "k_tc (gna_local_energy incremental, %s)" % prec_name,
+                         "achieved": achieved, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["bf16_tflops_sustained"],
+                         "peak_source": peak_kind + " bf16_tflops_sustained", "flops_per_launch": fl,
+                         "traffic": None},
+            "energy_vs_fp32_full": {"samples": nc, "rel_diff_mean": float(rel),
+                                    "rel_diff_per_sample_max": float(per_sample.max())}}
+
 
 def run_ours(a):
     import torch
@@ -357,9 +464,9 @@ def run_ours(a):
     prec_name = a.prec
     graph = gna.Graph.from_workload(g, L)
     if prec_name == "auto":
-        prec_name = "bf16"
+        prec_name = "bf16x2"
         try:
-            gna.workspace_size(graph, gna.Model(F, L, gna.PREC_BF16), gna.OP_ELOC_INCR, Bn)
+            gna.workspace_size(graph, gna.Model(F, L, gna.PREC_BF16X2), gna.OP_ELOC_INCR, Bn)
         except gna.GnaError:
             prec_name = "fp32"
     prec = {"bf16": gna.PREC_BF16, "bf16x2": gna.PREC_BF16X2, "fp32": gna.PREC_FP32}[prec_name]
@@ -370,6 +477,7 @@ def run_ours(a):
     chains = torch.tensor(W.random_spins(N, C, wl["spin_seed"] + 1000 * rank), device=dev)
     P = model.num_params
     lp = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
+    lp0 = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
     E = torch.empty((Bn, 2), dtype=torch.float64, device=dev)
     grad = torch.empty(P, dtype=torch.float64, device=dev)
     acc = torch.zeros(C, dtype=torch.int32, device=dev)
@@ -390,18 +498,19 @@ def run_ours(a):
                 marks.append((name, e))
 
         mark("start")
-        samples, lp0, _, _ = gna.metropolis_sweep(graph, model, theta, chains, S, 1, seed, state["step"] * S * N,
-                                                  n_accepted=acc, proposal=prop, eps=0.1)
+        samples, _, _, _ = gna.metropolis_sweep(graph, model, theta, chains, S, 1, seed, state["step"] * S * N,
+                                                n_accepted=acc, proposal=prop, eps=0.1, record_logpsi=False)
         s = samples.view(Bn, N)
-        l0 = lp0.view(Bn, 2)
         mark("metropolis_sweep")
         stats = None
-        for _ in range(K):
-            gna.forward(graph, model, theta, s, out=lp)
+        for k in range(K):
+            # log Psi^0: the first update's forward at the sampling parameters (weights exactly 1)
+            cur = lp0 if k == 0 else lp
+            gna.forward(graph, model, theta, s, out=cur)
             mark("forward")
             gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
             mark("local_energy")
-            cot, stats = gna.isgo_weights(lp, l0, E)
+            cot, stats = gna.isgo_weights(cur, lp0, E)
             mark("isgo_weights")
             gna.backward(graph, model_bwd, theta, s, cot, out=grad)
             gna.sgd_update(model, theta, grad, lr)
@@ -519,6 +628,26 @@ def run_ours(a):
     other = {"local_energy_tflops": fl_incr / (t_incr / 1000.0) / 1e12,
              "sweep_tflops": fl_sweep / (t_sweep / 1000.0) / 1e12}
 
+    # the single-BF16 (fast) local energy on the same samples: time, roofline, energy agreement
+    fast = None
+    if prec == gna.PREC_BF16X2:
+        model16 = gna.Model(F, L, gna.PREC_BF16)
+        t16 = time_call(lambda: gna.local_energy(graph, model16, theta, sub, gna.ELOC_INCREMENTAL, out=Esub))
+        E16 = gna.local_energy(graph, model16, theta, sub, gna.ELOC_INCREMENTAL).cpu().numpy()
+        fl_sub = float(incremental_flops(g, F, L, ball, deg, spins_np[:nc]).sum())
+        fast = {"dtype": "bf16", "eloc_samples_per_s": nc / (t16 / 1000.0),
+                "tflops": fl_sub / (t16 / 1000.0) / 1e12,
+                "frac": fl_sub / (t16 / 1000.0) / 1e12 / peaks["bf16_tflops_sustained"],
+                "energy_rel_diff_mean_vs_fp32_full": float(abs(E16[:, 0].mean() - E_full[:, 0].mean()) /
+                                                           abs(E_full[:, 0].mean())),
+                "energy_rel_diff_per_sample_max_vs_fp32_full": float((np.abs(E16[:, 0] - E_full[:, 0]) /
+                                                                      np.abs(E_full[:, 0]).clip(1e-12)).max())}
+    extras = {}
+    if rank == 0 and a.extra != "none":
+        for key in [k for k in a.extra.split(",") if k and k != a.workload]:
+            extras[key] = measure_workload(key, prec_name, dev, flush, 10 if key != "kagome432" else a.extra_reuse,
+                                           peaks, peak_kind)
+
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_oracle_rate(dict(wl, key=a.workload), n_per_worker=oracle_sample_size(dict(wl, key=a.workload)))
@@ -542,6 +671,8 @@ def run_ours(a):
                            "fp32_full_tflops": fl_full_sub / (t_full / 1000.0) / 1e12},
             "roofline": roof,
             "other_kernels": other,
+            "bf16_fast_local_energy": fast,
+            "extra_workloads": extras,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(C * N),
                     "d2h_bytes_per_step": 32},

@@ -57,7 +57,8 @@ typedef int32_t gna_status;
 #define GNA_ERR_NONFINITE (-4)     /* a non-finite value was produced (device status word) */
 #define GNA_ERR_WORKSPACE (-5)     /* the workspace is smaller than gna_workspace_size() */
 #define GNA_ERR_UNSUPPORTED (-6)   /* a valid request this build does not implement */
-#define GNA_WARN_DEGENERATE_WEIGHTS 1 /* ISGO effective sample size below 1% of the batch */
+#define GNA_WARN_DEGENERATE_WEIGHTS 1 /* ISGO effective sample size below 1% of the batch
+                                         (reported by gna_device_status) */
 
 /* Arithmetic of a call.  FP64: float64 everywhere (parity path).  FP32: float32
  * features, GEMMs and ratios.  BF16: the node-feature GEMM operands in bfloat16 on the
@@ -361,9 +362,24 @@ GNA_API gna_status gna_philox4x64_10(const uint64_t* keys, const uint64_t* count
                              uint64_t* out, void* stream);
 
 /* Reads and optionally clears the device status word of the current device: a bit mask
- * of conditions kernels recorded (1 = bounded wait timed out, 2 = non-finite value).
- * Synchronises the device. */
+ * of conditions kernels recorded since the last clear:
+ *   1  a bounded device-side wait gave up (the kernel left its outputs unwritten)
+ *   2  a non-finite value (ISGO statistics, or a tensor-core gradient)
+ *   4  degenerate importance weights: an ISGO weighting's effective sample size
+ *      1 / sum p^2/c fell below 1% of the copies in its batch (the paper warns that the
+ *      gradient then explodes; resample instead of reusing the samples)
+ * Kernels record these without a host synchronisation; this call synchronises the device.
+ * Returns the status of the most severe condition recorded: GNA_ERR_TIMEOUT (bit 1),
+ * GNA_ERR_NONFINITE (bit 2), GNA_WARN_DEGENERATE_WEIGHTS (bit 4), else GNA_OK; a failing
+ * CUDA call gives GNA_ERR_CUDA and leaves *flags unset. */
 GNA_API gna_status gna_device_status(int32_t* flags, int32_t clear);
+
+/* Test hook: the iteration limit of the bounded MMA waits of the tensor-core kernels
+ * launched from now on by this process (UINT32_MAX: the default, about 2 s).  With 0 every
+ * such wait gives up at once: the kernel records bit 1 of the device status word, waits
+ * with the default limit for the MMAs already issued, frees its tensor memory and returns,
+ * so the timeout path can be tested without a fault.  Not for production use. */
+GNA_API gna_status gna_debug_wait_limit(uint32_t iterations);
 
 #ifdef __cplusplus
 }

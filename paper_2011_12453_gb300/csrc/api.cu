@@ -474,5 +474,13 @@ extern "C" gna_status gna_device_status(int32_t* flags, int32_t clear) {
   st = tc_read_status(&f, clear);
   if (st != GNA_OK) return st;
   *flags = f;
+  if (f & 1) return GNA_ERR_TIMEOUT;
+  if (f & 2) return GNA_ERR_NONFINITE;
+  if (f & 4) return GNA_WARN_DEGENERATE_WEIGHTS;
+  return GNA_OK;
+}
+
+extern "C" gna_status gna_debug_wait_limit(uint32_t iterations) {
+  set_wait_limit(iterations);
   return GNA_OK;
 }

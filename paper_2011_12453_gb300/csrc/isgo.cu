@@ -90,12 +90,13 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_pass2(const double* lp, co
                                                             double* cot, double* part2) {
   __shared__ double sm[kRedThreads];
   const double m = gsum[0], S = gsum[1], er = gsum[2], ei = gsum[3];
-  double v = 0.0, q = 0.0;
+  double v = 0.0, q = 0.0, n = 0.0;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < B; x += (int64_t)gridDim.x * blockDim.x) {
     const double p = exp(log_weight(lp, lp0, counts, x) - m) / S;
     const double dr = E[2 * x] - er, di = E[2 * x + 1] - ei;
     v += p * (dr * dr + di * di);
     q += p * p / (counts ? counts[x] : 1.0);
+    n += counts ? counts[x] : 1.0;
     if (cot) {
       cot[2 * x] = 2.0 * p * dr;
       cot[2 * x + 1] = 2.0 * p * di;
@@ -103,28 +104,35 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_pass2(const double* lp, co
   }
   v = block_reduce<false>(v, sm);
   q = block_reduce<false>(q, sm);
+  n = block_reduce<false>(n, sm);
   if (threadIdx.x == 0) {
-    part2[2 * blockIdx.x] = v;
-    part2[2 * blockIdx.x + 1] = q;
+    part2[3 * blockIdx.x] = v;
+    part2[3 * blockIdx.x + 1] = q;
+    part2[3 * blockIdx.x + 2] = n;
   }
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_isgo_combine2(const double* part2, int nb, const double* gsum,
                                                                double* stats) {
   __shared__ double sm[kRedThreads];
-  double v = 0.0, q = 0.0;
+  double v = 0.0, q = 0.0, n = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    v += part2[2 * b];
-    q += part2[2 * b + 1];
+    v += part2[3 * b];
+    q += part2[3 * b + 1];
+    n += part2[3 * b + 2];
   }
   v = block_reduce<false>(v, sm);
   q = block_reduce<false>(q, sm);
+  n = block_reduce<false>(n, sm);
   if (threadIdx.x == 0) {
     stats[0] = gsum[2];
     stats[1] = gsum[3];
     stats[2] = v;
     stats[3] = 1.0 / q;
     if (!isfinite(gsum[2]) || !isfinite(gsum[3]) || !isfinite(v) || !isfinite(q)) atomicOr(&s_isgo_status, 2);
+    // degenerate reweighting (the failure the paper warns of: a few samples carry the
+    // weights and the gradient is dominated by them): IS-ESS below 1% of the copies
+    else if (1.0 / q < 0.01 * n) atomicOr(&s_isgo_status, 4);
   }
 }
 
@@ -137,7 +145,7 @@ static int isgo_blocks(int64_t B) {
 
 size_t isgo_weights_ws(int64_t B) {
   const int nb = isgo_blocks(B);
-  return align_up((size_t)nb * 4 * 8) + align_up((size_t)nb * 2 * 8) + align_up(4 * 8);
+  return align_up((size_t)nb * 4 * 8) + align_up((size_t)nb * 3 * 8) + align_up(4 * 8);
 }
 
 gna_status isgo_weights_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
@@ -147,7 +155,7 @@ gna_status isgo_weights_launch(const double* lp, const double* lp0, const double
   double* part = (double*)w;
   w += align_up((size_t)nb * 4 * 8);
   double* part2 = (double*)w;
-  w += align_up((size_t)nb * 2 * 8);
+  w += align_up((size_t)nb * 3 * 8);
   double* gsum = (double*)w;
   k_isgo_pass1<<<nb, kRedThreads, 0, st>>>(lp, lp0, counts, E, B, part);
   k_isgo_combine1<<<1, kRedThreads, 0, st>>>(part, nb, gsum);

@@ -29,6 +29,7 @@
 // status word, waits (bounded again) for the MMAs in flight, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <climits>
 #include <cstring>
 
@@ -81,9 +82,11 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// limit: try_wait iterations (a launch argument; kWaitLimit unless a test shortens it --
+// with 0 the wait gives up at once, which exercises the timeout path without a fault)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
   }
@@ -257,6 +260,7 @@ struct TcArgs {
   float* dlogpsi;
   unsigned char* gregion;  // [grid][region_bytes] when the region is not in shared memory
   int region_in_smem;
+  uint32_t wait_limit;     // try_wait iterations of the MMA waits (teardown waits keep kWaitLimit)
 };
 
 // Local energy and forward: F <= 32 two 256-thread units, wider features four 128-thread
@@ -572,7 +576,7 @@ __device__ bool run_mmas(const TcCtx& c, Unit& u, int nt) {
       }
     }
     mma_commit(u.bar);
-    const bool ok = mbar_wait_bounded(u.bar, u.phase);
+    const bool ok = mbar_wait_bounded(u.bar, u.phase, c.a->wait_limit);
     if (!ok) {
       *c.fail = 1;
       atomicOr(&s_tc_status, 1);
@@ -1902,10 +1906,10 @@ __device__ __forceinline__ void tcb_xchunk(const TcCtx& c, const float* Hs, int 
 }
 
 // Commit the MMAs issued by thread 0 and wait for them (bounded); false on timeout.
-__device__ __forceinline__ bool tcb_commit_wait(Unit& u, int* fail) {
+__device__ __forceinline__ bool tcb_commit_wait(Unit& u, int* fail, uint32_t limit) {
   if (threadIdx.x == 0) {
     mma_commit(u.bar);
-    if (!mbar_wait_bounded(u.bar, u.phase)) {
+    if (!mbar_wait_bounded(u.bar, u.phase, limit)) {
       *fail = 1;
       atomicOr(&s_tc_status, 1);
     }
@@ -1941,7 +1945,7 @@ __device__ bool tcb_forward(const TcCtx& c, Unit& u, float* Hs) {
         issue_mma(u.tbase, a_hi, wt, 2 * F, F, false);
         issue_mma(u.tbase, a_lo, wt, 2 * F, F, true);
       }
-      if (!tcb_commit_wait(u, c.fail)) return false;
+      if (!tcb_commit_wait(u, c.fail, c.a->wait_limit)) return false;
       const int q = q4 * 32 + lane;
       for (int ch = wg; ch < F8; ch += u.nwg) {
         float v[8];
@@ -2167,7 +2171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
           issue_mma(t_dx, a_hi, smem_u32(Wb), F, F2, false);
           issue_mma(t_dx, a_lo, smem_u32(Wb), F, F2, true);
         }
-        if (!tcb_commit_wait(u, c.fail)) {
+        if (!tcb_commit_wait(u, c.fail, c.a->wait_limit)) {
           ok = false;
           break;
         }
@@ -2281,11 +2285,18 @@ __global__ void k_tcb_reduce(const double* partial, int grid, int P, double* gra
   double s = 0.0;
   for (int cta = 0; cta < grid; ++cta) s += partial[(size_t)cta * P + p];
   grad[p] = s;
+  if (!isfinite(s)) atomicOr(&s_tc_status, 2);
 }
 
 // ---------------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------------
+// Iterations of the MMA waits of the kernels launched from now on (kWaitLimit; tests may
+// shorten it to exercise the timeout path).
+static std::atomic<uint32_t> g_wait_limit{kWaitLimit};
+void set_wait_limit(uint32_t iters) { g_wait_limit.store(iters == UINT32_MAX ? kWaitLimit : iters); }
+static uint32_t wait_limit() { return g_wait_limit.load(); }
+
 struct TcPlan {
   TcLayout lay;
   int grid = 0;
@@ -2395,6 +2406,7 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   a.dlogpsi = call.dlogpsi;
   a.gregion = (unsigned char*)ws;
   a.region_in_smem = p.region_in_smem;
+  a.wait_limit = wait_limit();
   if (call.split)
     k_tc<true><<<p.grid, kTcThreads, p.lay.smem_total, stream>>>(a);
   else
@@ -2559,6 +2571,7 @@ gna_status tcm_run(const TcmCall& call, void* ws, size_t ws_bytes, cudaStream_t 
   a.base.lay = p.lay;
   a.base.theta = call.theta;
   a.base.region_in_smem = p.new16_in_smem;  // here: where the units' dH rows live
+  a.base.wait_limit = wait_limit();
   a.chain_spins = call.chain_spins;
   a.C = call.C;
   a.n_sweeps = call.n_sweeps;
@@ -2718,6 +2731,7 @@ static gna_status tcb_launch(const TcbCall& call, void* ws, size_t ws_bytes, siz
   a.base.spins = call.spins;
   a.base.B = call.B;
   a.base.gregion = (unsigned char*)ws + p.partial_bytes;
+  a.base.wait_limit = wait_limit();
   a.cot = call.cot;
   a.partial = (double*)ws;
   k_tc_bwd<<<p.grid, kTcThreads, p.smem, stream>>>(a);

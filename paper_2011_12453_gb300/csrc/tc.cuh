@@ -56,5 +56,8 @@ gna_status tcm_workspace(const gna_graph* g, const Dims& m, int64_t C, size_t* b
 gna_status tcm_run(const TcmCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_run(const TcCall& c, void* ws, size_t ws_bytes, cudaStream_t stream);
 gna_status tc_read_status(int* flags, int clear);
+// Iterations of the bounded MMA waits of tensor-core kernels launched from now on
+// (UINT32_MAX: the default).
+void set_wait_limit(uint32_t iters);
 
 }  // namespace gna

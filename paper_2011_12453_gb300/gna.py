@@ -37,7 +37,7 @@ EXPORTED = [
     "gna_isgo_weights", "isgo_grad",
     "gna_sgd_update", "gna_philox4x64_10", "gna_device_status", "gna_proposal_num_params",
     "gna_proposal_workspace_size", "gna_proposal_logits", "gna_proposal_grad", "gna_proposal_adam",
-    "gna_dedup_workspace_size", "gna_dedup",
+    "gna_dedup_workspace_size", "gna_dedup", "gna_debug_wait_limit",
 ]
 
 
@@ -102,6 +102,7 @@ def lib():
             "gna_device_status": (i32, [ctypes.POINTER(i32), i32]),
             "gna_dedup_workspace_size": (i32, [i64, i32, ctypes.POINTER(sz)]),
             "gna_dedup": (i32, [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]),
+            "gna_debug_wait_limit": (i32, [ctypes.c_uint32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -288,19 +289,20 @@ def local_energy(graph: Graph, model: Model, theta, spins, mode: int = ELOC_INCR
 
 def metropolis_sweep(graph: Graph, model: Model, theta, chain_spins, n_sweeps: int, record_every: int, seed: int,
                      step0: int, trace: bool = False, n_accepted=None, records: bool = True, proposal=None,
-                     eps: float = 0.1):
+                     eps: float = 0.1, record_logpsi: bool = True):
     """Advance the chains in place; returns (samples [R][C][N] int8, logpsi [R][C][2], n_accepted [C], trace).
 
     proposal: float32 CUDA tensor of the proposal network's parameters (learned moves
     mixed with plain ones with probability eps) or None (plain moves).  trace rows are
-    (bond or -1, accepted, value, kind)."""
+    (bond or -1, accepted, value, kind).  record_logpsi=False records the samples only
+    (logpsi is then None)."""
     torch = _check_theta(model, theta)
     _check_spins(graph, chain_spins)
     C = chain_spins.shape[0]
     R = n_sweeps // record_every if (record_every > 0 and records) else 0
     dev = chain_spins.device
     samples = torch.empty((R, C, graph.n_sites), dtype=torch.int8, device=dev) if R else None
-    lpo = torch.empty((R, C, 2), dtype=torch.float64, device=dev) if R else None
+    lpo = torch.empty((R, C, 2), dtype=torch.float64, device=dev) if R and record_logpsi else None
     acc = n_accepted if n_accepted is not None else torch.zeros(C, dtype=torch.int32, device=dev)
     tr = torch.empty((C, n_sweeps * graph.n_sites, 4), dtype=torch.float64, device=dev) if trace else None
     op = OP_METROPOLIS_LEARNED if proposal is not None else OP_METROPOLIS
@@ -450,10 +452,21 @@ def philox(keys, counters):
     return out
 
 
-def device_status(clear: bool = True) -> int:
+def device_status(clear: bool = True, with_status: bool = False):
+    """Bit mask of the conditions kernels recorded (1 wait timed out, 2 non-finite, 4
+    degenerate importance weights); with_status=True also returns the call's status (the
+    most severe condition as a gna_status code)."""
     f = i32(0)
-    _check(lib().gna_device_status(ctypes.byref(f), int(clear)), "gna_device_status")
-    return int(f.value)
+    st = lib().gna_device_status(ctypes.byref(f), int(clear))
+    if st == GNA_ERR_CUDA:
+        _check(st, "gna_device_status")
+    return (int(f.value), int(st)) if with_status else int(f.value)
+
+
+def debug_wait_limit(iterations: int | None) -> None:
+    """Test hook: iteration limit of the tensor-core kernels' MMA waits (None: the default)."""
+    _check(lib().gna_debug_wait_limit(ctypes.c_uint32(0xFFFFFFFF if iterations is None else iterations)),
+           "gna_debug_wait_limit")
 
 
 # ---------------------------------------------------------------------------------

@@ -41,8 +41,11 @@ class Chains:
 def isgo_iteration(chains: Chains, K: int, lr: float, sweeps: int = 1, group: bool = False):
     """One ISGO iteration: `sweeps` sweeps then one recorded sample per chain, reused for K
     updates of theta; with group=True duplicated samples are first grouped into unique
-    states with counts (scaling section).  Returns the statistics [K][4] (Re E, Im E, var,
-    ESS) on the host."""
+    states with counts (scaling section).  log Psi^0 is the sampler's record, except for
+    the tensor-core precisions, whose sampler computes in BF16 while the forward may not
+    (BF16X2): there it is evaluated by the forward at the sampling parameters, the function
+    that evaluates log Psi at the later parameters, so that the weights are 1 at theta^0.
+    Returns the statistics [K][4] (Re E, Im E, var, ESS) on the host."""
     import torch
 
     samples, lp0, _, _ = chains.sweep(sweeps, record_every=sweeps)
@@ -52,6 +55,8 @@ def isgo_iteration(chains: Chains, K: int, lr: float, sweeps: int = 1, group: bo
     if group:
         s, l0, counts = gna.dedup(s, l0)
         s, l0, counts = s.contiguous(), l0.contiguous(), counts.contiguous()
+    if chains.model.prec in (gna.PREC_BF16, gna.PREC_BF16X2):
+        l0 = gna.forward(chains.graph, chains.model, chains.theta, s)
     stats = torch.empty((K, 4), dtype=torch.float64, device=s.device)
     grad = torch.empty(chains.model.num_params, dtype=torch.float64, device=s.device)
     for k in range(K):

@@ -10,6 +10,8 @@ import pytest
 from oracle import gcn, heisenberg as hz, isgo
 from paper_2011_12453_gb300 import build as B, gna, workloads as W
 
+import scales as SC
+
 pytestmark = pytest.mark.gpu
 
 
@@ -33,9 +35,13 @@ def _case(name):
     return g, {"bosons": hz.hardcore_bosons(E, 1.0, 2.5), "random": _random_xxz(E, 3)}
 
 
-def _close(got, want, tol):
-    err = np.abs(np.asarray(got) - np.asarray(want)).max()
-    assert err <= tol * max(np.abs(want).max(), 1.0), err
+def _close(got, want, tol, scale=None):
+    """Element by element: |got - want| <= tol * max(scale, 1), scale = |want| unless given (the
+    magnitude of the terms the value is summed from, tests/scales.py)."""
+    got, want = np.asarray(got), np.asarray(want)
+    err = np.abs(got - want)
+    lim = tol * np.maximum(np.abs(want) if scale is None else scale, 1.0)
+    assert np.all(err <= lim), (float(np.max(err - lim)), float(err.max()))
 
 
 @pytest.mark.parametrize("prec", [gna.PREC_FP64, gna.PREC_FP32])
@@ -57,7 +63,8 @@ def test_xxz_local_energy_parity(torch, prec, mode, name, kind):
         s = W.random_spins(g.n_sites, 17, seed=n_up, n_up=n_up)
         E = gna.local_energy(graph, model, theta, torch.tensor(s, device="cuda"), mode).cpu().numpy()
         want = hz.local_energy(lambda x: gcn.logpsi_complex(th_used, F, L, Ah, x), g.edges, None, s, xxz)
-        _close(E[:, 0] + 1j * E[:, 1], want, 1e-10 if prec == gna.PREC_FP64 else 1e-5)
+        _close(E[:, 0] + 1j * E[:, 1], want, 1e-10 if prec == gna.PREC_FP64 else 1e-5,
+               SC.eloc_scale(th_used, F, L, Ah, g.edges, None, s, xxz=xxz))
 
 
 def test_heisenberg_coefficients_reproduce_the_heisenberg_graph(torch):
@@ -114,6 +121,7 @@ def test_xxz_isgo_grad_parity(torch, prec):
     grad, stats = gna.isgo_grad(graph, model, theta, torch.tensor(s, device="cuda"), torch.tensor(lp0, device="cuda"))
     g_o, Ebar, var, ess, E, p = isgo.isgo_gradient(th, F, L, Ah, g.edges, None, s, lp0[:, 0] + 1j * lp0[:, 1],
                                                    xxz=xxz)
-    tol = 1e-9 if prec == gna.PREC_FP64 else 1e-4
-    _close(grad.cpu().numpy(), g_o, tol)
-    _close(stats.cpu().numpy()[:2], [Ebar.real, Ebar.imag], tol)
+    tol = 1e-10 if prec == gna.PREC_FP64 else 1e-5
+    _close(grad.cpu().numpy(), g_o, tol, SC.grad_scale(th, F, L, Ah, s, isgo.cotangents(p, E, Ebar)))
+    _close(stats.cpu().numpy()[:2], [Ebar.real, Ebar.imag], tol,
+           float((p * SC.eloc_scale(th, F, L, Ah, g.edges, None, s, xxz=xxz)).sum()))

@@ -9,6 +9,8 @@ import pytest
 from oracle import gcn, heisenberg as hz, isgo
 from paper_2011_12453_gb300 import build as B, gna, workloads as W
 
+import scales as SC
+
 pytestmark = pytest.mark.gpu
 
 
@@ -21,9 +23,13 @@ def torch():
     return t
 
 
-def _close(got, want, tol):
-    err = np.abs(np.asarray(got) - np.asarray(want)).max()
-    assert err <= tol * max(np.abs(want).max(), 1.0), err
+def _close(got, want, tol, scale=None):
+    """Element by element: |got - want| <= tol * max(scale, 1), scale = |want| unless given (the
+    magnitude of the terms the value is summed from, tests/scales.py)."""
+    got, want = np.asarray(got), np.asarray(want)
+    err = np.abs(got - want)
+    lim = tol * np.maximum(np.abs(want) if scale is None else scale, 1.0)
+    assert np.all(err <= lim), (float(np.max(err - lim)), float(err.max()))
 
 
 def _ah(g):
@@ -69,14 +75,15 @@ def test_isolated_site(torch, prec):
     s = W.random_spins(g.n_sites, 13, seed=3)
     st = torch.tensor(s, device="cuda")
     tol = 1e-10 if prec == gna.PREC_FP64 else 1e-5
-    _close(gna.forward(graph, model, theta, st).cpu().numpy(), gcn.logpsi(th, F, L, Ah, s), tol)
+    _close(gna.forward(graph, model, theta, st).cpu().numpy(), gcn.logpsi(th, F, L, Ah, s), tol,
+           SC.logpsi_scale(th, F, L, Ah, s))
     want = hz.local_energy(lambda x: gcn.logpsi_complex(th, F, L, Ah, x), g.edges, g.J, s)
     for mode in (gna.ELOC_FULL, gna.ELOC_INCREMENTAL):
         E = gna.local_energy(graph, model, theta, st, mode).cpu().numpy()
-        _close(E[:, 0] + 1j * E[:, 1], want, 10 * tol)
+        _close(E[:, 0] + 1j * E[:, 1], want, tol, SC.eloc_scale(th, F, L, Ah, g.edges, g.J, s))
     cot = np.random.default_rng(4).normal(size=(13, 2))
     got = gna.backward(graph, model, theta, st, torch.tensor(cot, device="cuda")).cpu().numpy()
-    _close(got, isgo.backward(th, F, L, Ah, s, cot), 1e-10 if prec == gna.PREC_FP64 else 1e-4)
+    _close(got, isgo.backward(th, F, L, Ah, s, cot), tol, SC.grad_scale(th, F, L, Ah, s, cot))
     ch = st.clone()
     gna.metropolis_sweep(graph, model, theta, ch, 2, 0, 5, 0)
     c = ch.cpu().numpy()

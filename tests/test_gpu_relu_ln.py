@@ -8,6 +8,8 @@ import pytest
 from oracle import gcn, heisenberg as hz, isgo, sampler
 from paper_2011_12453_gb300 import build as B, gna, workloads as W
 
+import scales as SC
+
 pytestmark = pytest.mark.gpu
 ACT = "relu_ln"
 TOL = {gna.PREC_FP64: 1e-10, gna.PREC_FP32: 1e-5}
@@ -37,9 +39,13 @@ def _geoms():
             "kagome6": W.kagome(6)}
 
 
-def _close(got, want, tol):
-    err = np.abs(np.asarray(got) - np.asarray(want)).max()
-    assert err <= tol * max(np.abs(want).max(), 1.0), err
+def _close(got, want, tol, scale=None):
+    """Element by element: |got - want| <= tol * max(scale, 1), scale = |want| unless given (the
+    magnitude of the terms the value is summed from, tests/scales.py)."""
+    got, want = np.asarray(got), np.asarray(want)
+    err = np.abs(got - want)
+    lim = tol * np.maximum(np.abs(want) if scale is None else scale, 1.0)
+    assert np.all(err <= lim), (float(np.max(err - lim)), float(err.max()))
 
 
 @pytest.mark.parametrize("prec", [gna.PREC_FP64, gna.PREC_FP32])
@@ -52,7 +58,7 @@ def test_forward_parity(torch, prec, geom, shared):
     for Bn in (29, 1):
         s = W.random_spins(g.n_sites, Bn, seed=Bn)
         got = gna.forward(graph, model, theta, torch.tensor(s, device="cuda")).cpu().numpy()
-        _close(got, gcn.logpsi(th, F, L, Ah, s, shared, ACT), TOL[prec])
+        _close(got, gcn.logpsi(th, F, L, Ah, s, shared, ACT), TOL[prec], SC.logpsi_scale(th, F, L, Ah, s, shared, ACT))
 
 
 @pytest.mark.parametrize("prec", [gna.PREC_FP64, gna.PREC_FP32])
@@ -68,9 +74,12 @@ def test_boson_local_energy_parity(torch, prec, mode, geom):
     E, dl = gna.local_energy(graph, model, theta, torch.tensor(s, device="cuda"), mode, bonds=True)
     E = E.cpu().numpy()
     lp_fn = lambda x: gcn.logpsi_complex(th, F, L, Ah, x, True, ACT)  # noqa: E731
-    _close(E[:, 0] + 1j * E[:, 1], hz.local_energy(lp_fn, g.edges, None, s, xxz), TOL[prec] * 10)
+    _close(E[:, 0] + 1j * E[:, 1], hz.local_energy(lp_fn, g.edges, None, s, xxz), TOL[prec],
+           SC.eloc_scale(th, F, L, Ah, g.edges, None, s, act=ACT, xxz=xxz))
     d = hz.bond_log_ratios(lp_fn, g.edges, s)
-    _close(dl.cpu().numpy(), np.where(np.isnan(d.real), 0.0, d.real), 2e-5)
+    want_d = np.where(np.isnan(d.real), 0.0, d.real)
+    assert np.all(np.abs(dl.cpu().numpy() - want_d) <= TOL[prec] * np.maximum(SC.delta_scale(
+        th, F, L, Ah, g.edges, s, act=ACT), 1.0) + 2.0 ** -24 * np.abs(want_d))
 
 
 def test_metropolis_fp64_trajectories_match_oracle(torch):
@@ -106,7 +115,7 @@ def test_backward_parity(torch, prec, shared):
     cot = np.random.default_rng(1).normal(size=(37, 2))
     got = gna.backward(graph, model, theta, torch.tensor(s, device="cuda"), torch.tensor(cot, device="cuda"))
     want = isgo.backward(th, F, L, Ah, s, cot, shared, ACT)
-    _close(got.cpu().numpy(), want, 1e-10 if prec == gna.PREC_FP64 else 1e-4)
+    _close(got.cpu().numpy(), want, TOL[prec], SC.grad_scale(th, F, L, Ah, s, cot, shared, ACT))
 
 
 @pytest.mark.parametrize("prec", [gna.PREC_FP64, gna.PREC_FP32])
@@ -121,9 +130,10 @@ def test_boson_isgo_grad_parity(torch, prec):
     grad, stats = gna.isgo_grad(graph, model, theta, torch.tensor(s, device="cuda"), torch.tensor(lp0, device="cuda"))
     g_o, Ebar, var, ess, E, p = isgo.isgo_gradient(th, F, L, Ah, g.edges, None, s, lp0[:, 0] + 1j * lp0[:, 1],
                                                    xxz=xxz, act=ACT)
-    tol = 1e-9 if prec == gna.PREC_FP64 else 1e-4
-    _close(grad.cpu().numpy(), g_o, tol)
-    _close(stats.cpu().numpy()[:2], [Ebar.real, Ebar.imag], tol)
+    tol = TOL[prec]
+    _close(grad.cpu().numpy(), g_o, tol, SC.grad_scale(th, F, L, Ah, s, isgo.cotangents(p, E, Ebar), act=ACT))
+    _close(stats.cpu().numpy()[:2], [Ebar.real, Ebar.imag], tol,
+           float((p * SC.eloc_scale(th, F, L, Ah, g.edges, None, s, act=ACT, xxz=xxz)).sum()))
 
 
 def test_bf16_relu_ln_is_unsupported(torch):

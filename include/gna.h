@@ -293,6 +293,28 @@ GNA_API gna_status gna_isgo_weights(const double* logpsi, const double* logpsi0,
                             const double* counts, int64_t B, double* cot, double* stats,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/* The same weights and statistics for samples sharded over several processes (the scaling
+ * section's data-parallel workers: each holds a contiguous block of the chains' samples;
+ * the weight sums and energies are summed across workers, then the gradient).  Two calls
+ * per shard around the caller's all-reduces:
+ *   gna_isgo_partials: part dev float64 [4] out = (m, S, S_re, S_im) of this shard, with
+ *     m = max_x log w_x (log w as in gna_isgo_weights), S = sum_x exp(log w_x - m) and
+ *     S_re + i S_im = sum_x exp(log w_x - m) E_x.
+ *   The caller forms the global m (max over shards), rescales each shard's sums by
+ *   exp(m_shard - m), sums them over shards to (S, S_re, S_im) and passes
+ *   global = (m, S, S_re/S, S_im/S) (dev float64 [4]) to
+ *   gna_isgo_finish: p = exp(log w - m)/S, cot = 2 p (E - Ebar) (dev [B][2] or NULL) and
+ *     part dev float64 [3] out = (sum p |E - Ebar|^2, sum p^2/counts, sum counts) of this
+ *     shard; summed over shards they give var, 1/ess and the number of copies.
+ * The backward with these cotangents gives each shard's part of the gradient, summed over
+ * shards by the caller.  Workspace as gna_isgo_weights_workspace(B). */
+GNA_API gna_status gna_isgo_partials(const double* logpsi, const double* logpsi0, const double* eloc,
+                                     const double* counts, int64_t B, double* part, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+GNA_API gna_status gna_isgo_finish(const double* logpsi, const double* logpsi0, const double* eloc,
+                                   const double* counts, int64_t B, const double* global, double* cot,
+                                   double* part, void* workspace, size_t workspace_bytes, void* stream);
+
 /* One ISGO gradient (Eq. isgo) at parameters theta on samples drawn under theta0:
  * forward log Psi, incremental local energy, weights and statistics, and the backward
  * VJP with the cotangents, all on the device.

@@ -384,6 +384,24 @@ extern "C" gna_status gna_isgo_weights(const double* logpsi, const double* logps
   return isgo_weights_launch(logpsi, logpsi0, eloc, counts, B, cot, stats, workspace, (cudaStream_t)stream);
 }
 
+extern "C" gna_status gna_isgo_partials(const double* logpsi, const double* logpsi0, const double* eloc,
+                                        const double* counts, int64_t B, double* part, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+  if (B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!logpsi || !logpsi0 || !eloc || !part) return GNA_ERR_INVALID_ARG;
+  if (workspace_bytes < isgo_weights_ws(B) || !workspace) return GNA_ERR_WORKSPACE;
+  return isgo_partials_launch(logpsi, logpsi0, eloc, counts, B, part, workspace, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_isgo_finish(const double* logpsi, const double* logpsi0, const double* eloc,
+                                      const double* counts, int64_t B, const double* global, double* cot,
+                                      double* part, void* workspace, size_t workspace_bytes, void* stream) {
+  if (B < 1 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (!logpsi || !logpsi0 || !eloc || !global || !part) return GNA_ERR_INVALID_ARG;
+  if (workspace_bytes < isgo_weights_ws(B) || !workspace) return GNA_ERR_WORKSPACE;
+  return isgo_finish_launch(logpsi, logpsi0, eloc, counts, B, global, cot, part, workspace, (cudaStream_t)stream);
+}
+
 extern "C" gna_status isgo_grad(const gna_graph* g, const gna_model_desc* d, const void* theta, const int8_t* spins,
                                 const double* logpsi0, const double* counts, int64_t B, double* grad, double* stats,
                                 void* workspace, size_t workspace_bytes, void* stream) {

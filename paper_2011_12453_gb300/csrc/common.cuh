@@ -152,6 +152,10 @@ size_t isgo_weights_ws(int64_t B);
 gna_status isgo_weights_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
                                double* cot, double* stats, void* ws, cudaStream_t st);
 gna_status sgd_launch(int prec, void* theta, const double* grad, double lr, int P, cudaStream_t st);
+gna_status isgo_partials_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
+                                double* part4, void* ws, cudaStream_t st);
+gna_status isgo_finish_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
+                              const double* global4, double* cot, double* part3, void* ws, cudaStream_t st);
 gna_status philox_launch(const uint64_t* keys, const uint64_t* ctrs, int64_t n, uint64_t* out, cudaStream_t st);
 gna_status isgo_read_status(int* flags, int clear);
 

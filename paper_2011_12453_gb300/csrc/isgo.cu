@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_pass1(const double* lp, co
   }
 }
 
-// combine: g = (m, S, Re Ebar, Im Ebar)
-__global__ void __launch_bounds__(kRedThreads) k_isgo_combine1(const double* part, int nb, double* gsum) {
+// combine: g = (m, S, Re Ebar, Im Ebar), or with raw = 1 the shard's (m, S, S Re Ebar, S Im Ebar)
+__global__ void __launch_bounds__(kRedThreads) k_isgo_combine1(const double* part, int nb, double* gsum, int raw) {
   __shared__ double sm[kRedThreads];
   double m = -INFINITY;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmax(m, part[4 * b]);
@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_combine1(const double* par
   if (threadIdx.x == 0) {
     gsum[0] = m;
     gsum[1] = s;
-    gsum[2] = sr / s;
-    gsum[3] = si / s;
+    gsum[2] = raw ? sr : sr / s;
+    gsum[3] = raw ? si : si / s;
   }
 }
 
@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_pass2(const double* lp, co
   }
 }
 
+// stats = (Re Ebar, Im Ebar, var, ess), or with raw != NULL the shard's sums (var, q, n) only
 __global__ void __launch_bounds__(kRedThreads) k_isgo_combine2(const double* part2, int nb, const double* gsum,
-                                                               double* stats) {
+                                                               double* stats, double* raw) {
   __shared__ double sm[kRedThreads];
   double v = 0.0, q = 0.0, n = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -124,7 +125,11 @@ __global__ void __launch_bounds__(kRedThreads) k_isgo_combine2(const double* par
   v = block_reduce<false>(v, sm);
   q = block_reduce<false>(q, sm);
   n = block_reduce<false>(n, sm);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && raw) {
+    raw[0] = v;
+    raw[1] = q;
+    raw[2] = n;
+  } else if (threadIdx.x == 0) {
     stats[0] = gsum[2];
     stats[1] = gsum[3];
     stats[2] = v;
@@ -158,9 +163,31 @@ gna_status isgo_weights_launch(const double* lp, const double* lp0, const double
   w += align_up((size_t)nb * 3 * 8);
   double* gsum = (double*)w;
   k_isgo_pass1<<<nb, kRedThreads, 0, st>>>(lp, lp0, counts, E, B, part);
-  k_isgo_combine1<<<1, kRedThreads, 0, st>>>(part, nb, gsum);
+  k_isgo_combine1<<<1, kRedThreads, 0, st>>>(part, nb, gsum, 0);
   k_isgo_pass2<<<nb, kRedThreads, 0, st>>>(lp, lp0, counts, E, B, gsum, cot, part2);
-  k_isgo_combine2<<<1, kRedThreads, 0, st>>>(part2, nb, gsum, stats);
+  k_isgo_combine2<<<1, kRedThreads, 0, st>>>(part2, nb, gsum, stats, nullptr);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+// Sample-sharded form: the shard's (m, S, S Re Ebar, S Im Ebar) ...
+gna_status isgo_partials_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
+                                double* part4, void* ws, cudaStream_t st) {
+  const int nb = isgo_blocks(B);
+  double* part = (double*)ws;
+  k_isgo_pass1<<<nb, kRedThreads, 0, st>>>(lp, lp0, counts, E, B, part);
+  k_isgo_combine1<<<1, kRedThreads, 0, st>>>(part, nb, part4, 1);
+  GNA_CUDA_TRY(cudaGetLastError());
+  return GNA_OK;
+}
+
+// ... and, given the global (m, S, Re Ebar, Im Ebar), the shard's cotangents and (var, q, n) sums.
+gna_status isgo_finish_launch(const double* lp, const double* lp0, const double* E, const double* counts, int64_t B,
+                              const double* global4, double* cot, double* part3, void* ws, cudaStream_t st) {
+  const int nb = isgo_blocks(B);
+  double* part2 = (double*)ws;
+  k_isgo_pass2<<<nb, kRedThreads, 0, st>>>(lp, lp0, counts, E, B, global4, cot, part2);
+  k_isgo_combine2<<<1, kRedThreads, 0, st>>>(part2, nb, global4, nullptr, part3);
   GNA_CUDA_TRY(cudaGetLastError());
   return GNA_OK;
 }

@@ -38,6 +38,7 @@ EXPORTED = [
     "gna_sgd_update", "gna_philox4x64_10", "gna_device_status", "gna_proposal_num_params",
     "gna_proposal_workspace_size", "gna_proposal_logits", "gna_proposal_grad", "gna_proposal_adam",
     "gna_dedup_workspace_size", "gna_dedup", "gna_debug_wait_limit",
+    "gna_isgo_partials", "gna_isgo_finish",
 ]
 
 
@@ -103,6 +104,8 @@ def lib():
             "gna_dedup_workspace_size": (i32, [i64, i32, ctypes.POINTER(sz)]),
             "gna_dedup": (i32, [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]),
             "gna_debug_wait_limit": (i32, [ctypes.c_uint32]),
+            "gna_isgo_partials": (i32, [vp, vp, vp, vp, i64, vp, vp, sz, vp]),
+            "gna_isgo_finish": (i32, [vp, vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -398,6 +401,36 @@ def isgo_weights(logpsi, logpsi0, eloc, counts=None):
                                   cot.data_ptr(), stats.data_ptr(), w.data_ptr(), w.numel(), _stream()),
            "gna_isgo_weights")
     return cot, stats
+
+
+def isgo_partials(logpsi, logpsi0, eloc, counts=None):
+    """This shard's (m, S, S Re Ebar, S Im Ebar): float64 [4] on the device."""
+    import torch
+
+    B = logpsi.shape[0]
+    part = torch.empty(4, dtype=torch.float64, device=logpsi.device)
+    need = sz(0)
+    _check(lib().gna_isgo_weights_workspace(B, ctypes.byref(need)), "gna_isgo_weights_workspace")
+    w = workspace(int(need.value))
+    _check(lib().gna_isgo_partials(logpsi.data_ptr(), logpsi0.data_ptr(), eloc.data_ptr(), _ptr(counts), B,
+                                   part.data_ptr(), w.data_ptr(), w.numel(), _stream()), "gna_isgo_partials")
+    return part
+
+
+def isgo_finish(logpsi, logpsi0, eloc, global4, counts=None):
+    """(cot [B][2], (sum p |E - Ebar|^2, sum p^2/c, sum c) [3]) of this shard on the device."""
+    import torch
+
+    B = logpsi.shape[0]
+    cot = torch.empty((B, 2), dtype=torch.float64, device=logpsi.device)
+    part = torch.empty(3, dtype=torch.float64, device=logpsi.device)
+    need = sz(0)
+    _check(lib().gna_isgo_weights_workspace(B, ctypes.byref(need)), "gna_isgo_weights_workspace")
+    w = workspace(int(need.value))
+    _check(lib().gna_isgo_finish(logpsi.data_ptr(), logpsi0.data_ptr(), eloc.data_ptr(), _ptr(counts), B,
+                                 global4.data_ptr(), cot.data_ptr(), part.data_ptr(), w.data_ptr(), w.numel(),
+                                 _stream()), "gna_isgo_finish")
+    return cot, part
 
 
 def isgo_grad(graph: Graph, model: Model, theta, spins, logpsi0, counts=None, grad=None, stats=None):

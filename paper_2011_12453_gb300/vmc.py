@@ -102,12 +102,14 @@ def tau_int(x: np.ndarray, c: float = 5.0) -> float:
     return float(tau)
 
 
-def energy_series(chains: Chains, n_sweeps: int, proposal=None, eps: float = 0.1):
+def energy_series(chains: Chains, n_sweeps: int, proposal=None, eps: float = 0.1, energy_model=None):
     """Local energy of every chain after each of n_sweeps sweeps: (E [n_sweeps][C] float64,
-    device seconds spent sampling)."""
+    device seconds spent sampling).  energy_model: the model (precision) of the local
+    energies, default the chains' own."""
     import torch
 
-    graph, model, theta = chains.graph, chains.model, chains.theta
+    graph, theta = chains.graph, chains.theta
+    model = chains.model if energy_model is None else energy_model
     C = chains.spins.shape[0]
     series = np.empty((n_sweeps, C))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -103,6 +103,71 @@ def test_learned_metropolis_fp64_matches_oracle(torch):
     assert np.array_equal(acc.cpu().numpy(), acc_o)
 
 
+def test_learned_metropolis_fp64_matches_oracle_irregular(torch):
+    # an irregular random graph (degrees 2..6): moves, decisions and log acceptance ratios
+    # of the learned-move chains equal the oracle's step for step
+    g = W.erdos_renyi(14, 0.3, seed=11, J_range=(0.5, 1.5))
+    F, L = 8, 2
+    th = W.random_theta(F, L, seed=3, scale=0.8)
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_FP64)
+    theta = torch.tensor(th, device="cuda")
+    p32, pnp = _params(torch, 6, scale=1.0)
+    Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
+    C, sweeps, seed, step0, eps = 8, 3, 91, 3, 0.2
+    s0 = W.random_spins(g.n_sites, C, seed=9)
+    ch = torch.tensor(s0, device="cuda")
+    _, _, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, sweeps, 0, seed, step0, trace=True, proposal=p32,
+                                         eps=eps)
+    top = P.Topology(g.n_sites, g.edges, g.J)
+    s_o, acc_o, tr_o = P.run_chains(lambda x: gcn.logpsi_complex(th, F, L, Ah, np.atleast_2d(x)), top, pnp, s0, seed,
+                                    step0, sweeps, eps)
+    tr = tr.cpu().numpy()
+    deg = np.bincount(g.edges.ravel(), minlength=g.n_sites)
+    assert deg.min() < deg.max()
+    for c in range(C):
+        for k in range(tr.shape[1]):
+            kind, i, j, ok, lr = tr_o[c, k]
+            assert tr[c, k, 3] == kind, (c, k)
+            e = top.bond[(int(i), int(j))] if j >= 0 else -1
+            assert tr[c, k, 0] == e, (c, k)
+            assert tr[c, k, 1] == ok, (c, k)
+            if np.isnan(lr):
+                assert np.isnan(tr[c, k, 2])
+            else:
+                assert abs(tr[c, k, 2] - lr) < 1e-9, (c, k, tr[c, k, 2], lr)
+    assert np.array_equal(ch.cpu().numpy(), s_o)
+    assert np.array_equal(acc.cpu().numpy(), acc_o)
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_fp32_samplers_reproduce_the_exact_energy_irregular(torch, learned):
+    # 12-site irregular random graph, a structured psi (weight scale 0.5: the largest |psi|^2
+    # is 7 % of the total, an effective support of ~70 of the 924 sector states): after 100
+    # sweeps of warm-up the chains' mean local energy equals the exact <psi|H|psi>/<psi|psi>
+    # within 5 standard errors, for plain and for learned moves on the FP32 warp sampler
+    from paper_2011_12453_gb300 import vmc
+
+    g = W.erdos_renyi(12, 0.35, seed=21, J_range=(0.5, 1.5))
+    F, L, C = 16, 2, 2048
+    graph = gna.Graph.from_workload(g, L)
+    model = gna.Model(F, L, gna.PREC_FP32)
+    theta = torch.tensor(W.random_theta(F, L, seed=5, scale=0.5), dtype=torch.float32, device="cuda")
+    th = theta.double().cpu().numpy()
+    Ah = gcn.norm_adjacency(gcn.adjacency(g.n_sites, g.edges))
+    Hs, codes = hz.sector_hamiltonian(g.n_sites, g.edges, g.J)
+    sall = hz.codes_to_spins(codes, g.n_sites)
+    Ev = hz.variational_energy(gcn.logpsi_complex(th, F, L, Ah, sall), Hs).real
+    p32, _ = _params(torch, 7, scale=1.0)
+    ch = vmc.Chains(graph, model, theta, W.random_spins(g.n_sites, C, seed=3), seed=13)
+    prop = p32 if learned else None
+    ch.sweep(100, proposal=prop)
+    series, _ = vmc.energy_series(ch, 100, proposal=prop)
+    means = series.mean(axis=0)
+    err = means.std() / np.sqrt(C)
+    assert abs(series.mean() - Ev) < 5 * err + 1e-6, (series.mean(), Ev, err)
+
+
 def test_learned_metropolis_conserves_sz_and_stays_finite(torch):
     g = W.erdos_renyi(40, 0.1, seed=7, J_range=(0.5, 1.5))
     F, L = 16, 3

@@ -62,9 +62,11 @@ def _layers_and_pre(th, F, L, Ah, spins):
     return H, Y
 
 
-def bond_bounds(th, F, L, Ah, edges, J, spins, mode):
+def bond_bounds(th, F, L, Ah, edges, J, spins, mode, parts=False):
     """For each sample and bond: the exact Delta = log Psi(s^e) - log Psi(s) (complex, NaN on
-    parallel bonds), the bound on |err Delta| and the per-sample bound on |err E_loc|."""
+    parallel bonds), the bound on |err Delta| and the per-sample bound on |err E_loc|; with
+    parts=True also, per sample, the local-energy error's shared part (an absolute bound)
+    and the standard deviation of its independent part, to first order."""
     u_s, u_a, u_t = UNITS[mode]
     p = gcn.unpack(th, F, L)
     wr = p["w_r"][:F]
@@ -91,6 +93,8 @@ def bond_bounds(th, F, L, Ah, edges, J, spins, mode):
     delta = np.full((B, E), np.nan + 0j)
     bound = np.zeros((B, E))
     e_bound = np.zeros(B)
+    e_shared = np.zeros(B)
+    e_sigma = np.zeros(B)
     for b in range(B):
         s = spins[b]
         anti = np.nonzero(s[edges[:, 0]] != s[edges[:, 1]])[0]
@@ -120,6 +124,14 @@ def bond_bounds(th, F, L, Ah, edges, J, spins, mode):
         bound[b, anti] = bd
         amp = np.abs(np.exp(d[:, 0] + 1j * d[:, 1]))
         e_bound[b] = float((0.5 * np.abs(np.asarray(J)[anti]) * amp * np.expm1(bd)).sum())
+        # the sample's local-energy error as a shared part (bounded in absolute value, summed
+        # over bonds) and an independent part (standard deviation, added in quadrature)
+        shr = np.abs(sgn.sum(axis=1) @ wr).sum(axis=1)
+        w = 0.5 * np.abs(np.asarray(J)[anti]) * amp
+        e_shared[b] = float((w * shr).sum())
+        e_sigma[b] = float(np.sqrt(((w * sig) ** 2).sum()))
+    if parts:
+        return delta, bound, e_bound, e_shared, e_sigma
     return delta, bound, e_bound
 
 

@@ -233,6 +233,8 @@ struct TcLayout {
   uint32_t row_unit, pos_unit;    // staged rows (int) / neighbour positions (int16) per unit
   // region (shared or global) byte offsets
   uint64_t rcache16, rY, rnew16, rpart, region_bytes;
+  int y_global;                   // 1: the Y cache in the workspace (y_bytes per CTA), not in the region
+  uint64_t y_bytes;
   uint64_t new16_off[kMaxL + 1];  // per layer l < L: offset of the group's dH rows (bytes from rnew16)
   int T;                          // A tiles per unit (TMEM holds T accumulators of F columns per unit)
   int split;                      // 1: operands as hi + lo BF16 pairs, FP32 feature rows
@@ -259,6 +261,7 @@ struct TcArgs {
   double* eloc;
   float* dlogpsi;
   unsigned char* gregion;  // [grid][region_bytes] when the region is not in shared memory
+  float* gY;               // [grid][y_bytes] when lay.y_global
   int region_in_smem;
   uint32_t wait_limit;     // try_wait iterations of the MMA waits (teardown waits keep kWaitLimit)
 };
@@ -302,7 +305,7 @@ __host__ inline void tc_stage_layout(const Dims& m, const int* maxball, int maxs
 // alias_new16: the group rows' dH layers share the space of the BF16 layer cache, which
 // only the forward reads (the incremental step needs the pre-activations alone).
 __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, int G, int region_in_smem,
-                               int alias_new16, TcLayout* t, int split = 0) {
+                               int alias_new16, TcLayout* t, int split = 0, int y_global = 0) {
   const int F = m.F, N = m.N, L = m.L;
   uint64_t o = 0;
   auto take = [&](uint64_t bytes, uint64_t align) {
@@ -343,7 +346,11 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
   const uint64_t ldh = F + 8, ldy = F + 4;  // padded row strides (BF16 rows, FP32 rows)
   // feature rows of the layer cache and of the dH rows: BF16, or FP32 when split
   const uint64_t row_bytes = split ? ldy * 4 : ldh * 2;
-  t->rY = rtake((uint64_t)L * N * ldy * 4);  // Y^1..Y^L (FP32); the forward-only call keeps H^L there
+  // Y^1..Y^L (FP32; the forward-only call keeps H^L there): in the region, or in the
+  // workspace (L2-resident) when that lets more bonds share a group
+  t->y_global = y_global;
+  t->y_bytes = ((uint64_t)L * N * ldy * 4 + 255) / 256 * 256;
+  t->rY = y_global ? 0 : rtake((uint64_t)L * N * ldy * 4);
   uint64_t n16 = 0;
   for (int l = 0; l < L; ++l) {
     t->new16_off[l] = n16;
@@ -387,6 +394,7 @@ struct TcCtx {
   int* list;     // antiparallel bonds of the configuration
   double* sdbl;  // shared double scratch (readout)
   unsigned char* region;
+  float* ycache; // Y^1..Y^L of the configuration (region or workspace)
   int* fail;     // shared flag
 };
 
@@ -464,7 +472,7 @@ __device__ __forceinline__ __nv_bfloat16* cache16w(const TcCtx& c, int l) {
 // Per site and layer l = 1..L: copysign(exp(-2|Y^l|), Y^l) for the incremental step (Y^l
 // the FP32 pre-activation); for the forward-only call the last slot holds H^L instead.
 __device__ __forceinline__ float* cacheY(const TcCtx& c, int l) {
-  return (float*)(c.region + c.a->lay.rY) + (size_t)(l - 1) * c.N * c.ldy;
+  return c.ycache + (size_t)(l - 1) * c.N * c.ldy;
 }
 __device__ __forceinline__ __nv_bfloat16* new16(const TcCtx& c, const Unit& u, int l) {
   return (__nv_bfloat16*)((unsigned char*)u.d16 + c.a->lay.new16_off[l]);
@@ -1029,6 +1037,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   c.list = (int*)(smem + a.lay.oint);
   c.sdbl = (double*)(smem + a.lay.odbl);
   c.region = a.region_in_smem ? smem + a.lay.oregion : a.gregion + (size_t)blockIdx.x * a.lay.region_bytes;
+  c.ycache = a.lay.y_global ? a.gY + (size_t)blockIdx.x * (a.lay.y_bytes / 4) : (float*)(c.region + a.lay.rY);
   c.fail = &s_fail;
   const int F = c.F, N = c.N;
   const Dims& m = a.m;
@@ -1492,6 +1501,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_metro(const TcmArgs a) {
   c.list = (int*)(smem + b.lay.oint);
   c.sdbl = (double*)(smem + b.lay.odbl);
   c.region = smem + b.lay.oregion;
+  c.ycache = (float*)(c.region + b.lay.rY);
   c.fail = &s_fail;
   const int F = c.F, N = c.N, L = c.L, G = c.G, E = c.E;
   const Dims& m = b.m;
@@ -1990,6 +2000,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
   c.list = (int*)(smem + b.lay.oint);
   c.sdbl = (double*)(smem + b.lay.odbl);
   c.region = b.region_in_smem ? smem + b.lay.oregion : b.gregion + (size_t)blockIdx.x * b.lay.region_bytes;
+  c.ycache = nullptr;  // the backward keeps its own FP32 layers
   c.fail = &s_fail;
   const int F = c.F, N = c.N, L = c.L, ldy = c.ldy;
   const int F8 = F / 8, F2 = 2 * F;
@@ -2324,19 +2335,24 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   // prefer the whole region in shared memory with as many bonds per group as fit (the dH
   // rows reuse the layer cache's space where they fit in it)
   // the group size with the fewest passes per bond (ties: the larger) among those that fit
-  int g_fit = 0, best = 1 << 30;
-  for (int gg = op == TC_ELOC ? 16 : 1; gg >= 1; --gg) {
-    tc_layout(m, maxball, maxspan, gg, 1, op == TC_ELOC, &lay, split);
-    if (lay.smem_total > budget) continue;
-    const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
-    if (cost < best) {
-      best = cost;
-      g_fit = gg;
+  // (with the Y cache in shared memory; moved to the workspace only when that allows
+  // strictly fewer passes per bond -- BF16X2 at Kagome 108: 7 bonds instead of 4)
+  int g_fit = 0, best = 1 << 30, y_glob = 0;
+  for (int yg = 0; yg <= (op == TC_ELOC ? 1 : 0); ++yg) {
+    for (int gg = op == TC_ELOC ? 16 : 1; gg >= 1; --gg) {
+      tc_layout(m, maxball, maxspan, gg, 1, op == TC_ELOC, &lay, split, yg);
+      if (lay.smem_total > budget) continue;
+      const int cost = tc_passes_per_bond(maxball, m.L, gg, T * 128);
+      if (cost < best) {
+        best = cost;
+        g_fit = gg;
+        y_glob = yg;
+      }
     }
   }
   if (g_fit > 0) {
     p->region_in_smem = 1;
-    tc_layout(m, maxball, maxspan, g_fit, 1, op == TC_ELOC, &lay, split);
+    tc_layout(m, maxball, maxspan, g_fit, 1, op == TC_ELOC, &lay, split, y_glob);
   } else {
     // region in the workspace: the group size by the same cost model among those that fit,
     // up to 8 bonds (larger groups spill the per-CTA regions out of L2: triangular 144,
@@ -2370,7 +2386,8 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (grid > B) grid = B;
   if (grid < 1) grid = 1;
   p->grid = (int)grid;
-  p->ws_bytes = p->region_in_smem ? 0 : align_up((size_t)grid * lay.region_bytes);
+  p->ws_bytes = (p->region_in_smem ? 0 : align_up((size_t)grid * lay.region_bytes)) +
+                (lay.y_global ? align_up((size_t)grid * lay.y_bytes) : 0);
   return GNA_OK;
 }
 
@@ -2405,6 +2422,7 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   a.eloc = call.eloc;
   a.dlogpsi = call.dlogpsi;
   a.gregion = (unsigned char*)ws;
+  a.gY = (float*)((unsigned char*)ws + (p.region_in_smem ? 0 : align_up((size_t)p.grid * p.lay.region_bytes)));
   a.region_in_smem = p.region_in_smem;
   a.wait_limit = wait_limit();
   if (call.split)

@@ -85,6 +85,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // limit: try_wait iterations (a launch argument; kWaitLimit unless a test shortens it --
 // with 0 the wait gives up at once, which exercises the timeout path without a fault)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+  if (limit > 0 && mbar_try_wait(bar, parity)) return true;  // the usual case, before reading the timer
   const uint64_t t0 = global_ns();
   for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -328,9 +329,9 @@ __host__ inline bool tc_layout(const Dims& m, const int* maxball, int maxspan, i
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
   t->ospin = take(N, 16);
-  t->int_unit = (uint32_t)(G + (L + 2) * (G + 1) + 4);
+  t->int_unit = (uint32_t)(3 * G + (L + 2) * (G + 1) + 4);
   t->oint = take(((uint64_t)m.E + 16 + (uint64_t)U * t->int_unit) * 4, 16);
-  t->dbl_unit = (uint32_t)(2 * G + 4);
+  t->dbl_unit = (uint32_t)(3 * G + 64 + 4);  // Delta [2G], couplings [G], lane sums [2 x 32]
   t->odbl = take((uint64_t)(16 + kTcThreads + U * t->dbl_unit) * 8, 16);
   t->obar = take(8 * U, 8);
   t->oslot = take(4, 4);
@@ -411,7 +412,8 @@ struct Unit {
   float* part;                 // this unit's Delta partials [nwg][T*128][2]
   int* slot_e;                 // [G]
   int* soff;                   // [(L+1)][G+1]
-  int* eoff;                   // [G+1] start of each bond's staged neighbour positions
+  int* eoff;                   // [G+1] start of each bond's staged neighbour positions, then
+                               // [G] + [G] each bond's start in row_pack and in nbr_pos16
   int* srow;                   // staged row_pack of the group's bonds (bond k at soff[L][k])
   int16_t* spos;               // staged nbr_pos16 of the group's bonds (bond k at eoff[k])
   double* res;                 // [2G] Delta of each bond of the group
@@ -424,36 +426,93 @@ __device__ __forceinline__ void unit_sync(const Unit& u) {
     asm volatile("bar.sync %0, %1;" ::"r"(u.bar_id), "r"(u.nthr) : "memory");
 }
 
+// Slot of group row q at layer l (offsets offl[0..nb]).
+// Branch-free binary search for the largest k < nb with offl[k] <= q (offl strictly
+// increasing, offl[0] = 0 <= q; nb <= 16).
+__device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
+  int k = 0;
+#pragma unroll
+  for (int step = 8; step >= 1; step >>= 1) {
+    const int j = k + step;
+    if (j < nb && offl[j] <= q) k = j;
+  }
+  return k;
+}
+
 // Offsets of the group's rows per layer (soff) and of its bonds' staged entries (eoff),
 // then the bonds' rows and in-ball neighbour positions into shared memory, so that the
-// passes of the group look them up without global-memory latency.
-__device__ void stage_group(const DevGraph& g, const Unit& u, int L, int G, int nb) {
+// passes of the group look them up without global-memory latency.  Every step is one
+// parallel loop (the group's G <= 16 bonds are the lanes of one warp in the prefix sums), so
+// the staging costs a few global-load latencies, not one per bond.
+// Jout (when not null): each bond's coupling, loaded in the same round.  NL: loads in flight
+// per thread in the copies.
+template <int NL>
+__device__ void stage_group(const DevGraph& g, const Unit& u, int L, int G, int nb, double* Jout = nullptr) {
   const int Lm = g.Lmax;
-  // sizes into the offset arrays (shifted by one), loaded in parallel ...
-  for (int i = u.tid; i < (L + 2) * nb; i += u.nthr) {
+  int* rbase = u.eoff + G + 1;
+  int* ebase = rbase + G;
+  // sizes into the offset arrays (shifted by one) and each bond's table starts ...
+  for (int i = u.tid; i < (L + 3 + (Jout ? 1 : 0)) * nb; i += u.nthr) {
     const int l = i / nb, k = i - l * nb;
-    const size_t eo = (size_t)u.slot_e[k] * (Lm + 1);
-    if (l <= L)
-      u.soff[l * (G + 1) + k + 1] = __ldg(g.ball_size + eo + l);
-    else
-      u.eoff[k + 1] = __ldg(g.ball_span + eo + L);
-  }
-  unit_sync(u);
-  // ... then prefix sums, one thread per array
-  if (u.tid <= L + 1) {
-    int* row = u.tid <= L ? u.soff + u.tid * (G + 1) : u.eoff;
-    row[0] = 0;
-    for (int k = 0; k < nb; ++k) row[k + 1] += row[k];
-  }
-  unit_sync(u);
-  const int* offL = u.soff + L * (G + 1);
-  for (int k = 0; k < nb; ++k) {
     const int e = u.slot_e[k];
-    const int* rows = g.row_pack + __ldg(g.ball_off + e);
-    const int16_t* ents = g.nbr_pos16 + __ldg(g.bond_ent + e);
-    const int nr = offL[k + 1] - offL[k], ne = u.eoff[k + 1] - u.eoff[k];
-    for (int r = u.tid; r < nr; r += u.nthr) u.srow[offL[k] + r] = __ldg(rows + r);
-    for (int t = u.tid; t < ne; t += u.nthr) u.spos[u.eoff[k] + t] = __ldg(ents + t);
+    const size_t eo = (size_t)e * (Lm + 1);
+    if (l <= L) {
+      u.soff[l * (G + 1) + k + 1] = __ldg(g.ball_size + eo + l);
+    } else if (l == L + 1) {
+      u.eoff[k + 1] = __ldg(g.ball_span + eo + L);
+    } else if (l == L + 2) {
+      rbase[k] = __ldg(g.ball_off + e);
+      ebase[k] = __ldg(g.bond_ent + e);
+    } else {
+      Jout[k] = __ldg(g.J + e);
+    }
+  }
+  unit_sync(u);
+  // ... then inclusive prefix sums, one warp per array, lane k holding bond k
+  const int warp = u.tid >> 5, lane = u.tid & 31, nwarps = u.nthr >> 5;
+  for (int w = warp; w <= L + 1; w += nwarps) {
+    int* row = w <= L ? u.soff + w * (G + 1) : u.eoff;
+    int x = lane < nb ? row[lane + 1] : 0;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane < nb) row[lane + 1] = x;
+    if (lane == 0) row[0] = 0;
+  }
+  unit_sync(u);
+  // ... then the rows and positions of all bonds in one loop each
+  // (NL loads in flight per thread before their stores)
+  const int* offL = u.soff + L * (G + 1);
+  const int nr = offL[nb], ne = u.eoff[nb];
+  for (int i0 = u.tid; i0 < nr; i0 += NL * u.nthr) {
+    int v[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int i = i0 + j * u.nthr;
+      if (i < nr) {
+        const int k = slot_of(offL, nb, i);
+        v[j] = __ldg(g.row_pack + rbase[k] + (i - offL[k]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+      if (i0 + j * u.nthr < nr) u.srow[i0 + j * u.nthr] = v[j];
+  }
+  for (int i0 = u.tid; i0 < ne; i0 += NL * u.nthr) {
+    int16_t v[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int i = i0 + j * u.nthr;
+      if (i < ne) {
+        const int k = slot_of(u.eoff, nb, i);
+        v[j] = __ldg(g.nbr_pos16 + ebase[k] + (i - u.eoff[k]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+      if (i0 + j * u.nthr < ne) u.spos[i0 + j * u.nthr] = v[j];
   }
 }
 
@@ -741,24 +800,11 @@ __device__ void tc_readout(const TcCtx& c, double out[2]) {
   __syncthreads();
 }
 
-// Slot of group row q at layer l (offsets offl[0..nb]).
-// Branch-free binary search for the largest k < nb with offl[k] <= q (offl strictly
-// increasing, offl[0] = 0 <= q; nb <= 16).
-__device__ __forceinline__ int slot_of(const int* offl, int nb, int q) {
-  int k = 0;
-#pragma unroll
-  for (int step = 8; step >= 1; step >>= 1) {
-    const int j = k + step;
-    if (j < nb && offl[j] <= q) k = j;
-  }
-  return k;
-}
-
 // dX rows of a bond group at layer l, gathered into the unit's A tiles:
 //   [ sum_{u in N(v), u in ball_{l-1}} w_vu dH^{l-1}_u ; dH^{l-1}_v (0 outside ball_{l-1}) ]
-// One thread per (row, 8-feature chunk): the chunk of the message and the chunk of the self
-// term, so that every thread of the unit does the same amount of work.  S: dH rows in FP32,
-// the gathered rows stored as hi + lo tiles.
+// One thread per (row, 16 features): the two 8-feature chunks of the message and of the self
+// term, the row's index lookups done once for both (every thread of the unit does the same
+// amount of work).  S: dH rows in FP32, the gathered rows stored as hi + lo tiles.
 template <bool S>
 __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q0, int n) {
   const int F = c.F, G = c.G, ldh = c.ldh;
@@ -767,80 +813,100 @@ __device__ void gather_delta(const TcCtx& c, const Unit& u, int l, int nb, int q
   const int* offl = u.soff + l * (G + 1);
   const int* offL = u.soff + c.L * (G + 1);
   const __nv_bfloat16* dp = new16(c, u, l - 1);
-  const int f8s = F8 == 2 ? 1 : F8 == 4 ? 2 : F8 == 8 ? 3 : -1;  // log2(F/8) when a power of two
-  for (int idx = u.tid; idx < n * F8; idx += u.nthr) {
-    const int qa = f8s >= 0 ? idx >> f8s : idx / F8, ch = idx - qa * F8, q = q0 + qa;
-    const int k = slot_of(offl, nb, q);
-    const int r = q - offl[k];
-    const int sprev = offp[k + 1] - offp[k];
-    const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh + ch * 8;
-    const int rec = u.srow[offL[k] + r];
-    const int v = rec & 0xFFFF;
-    const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
-    const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
-    if (S) {
+  const int F16 = F8 / 2;  // F is a multiple of 16
+  const int f16s = F16 == 1 ? 0 : F16 == 2 ? 1 : F16 == 4 ? 2 : -1;  // log2(F/16) when a power of two
+  if (S) {
+    const unsigned lo = c.a->lay.lo_off;
+    for (int idx = u.tid; idx < n * F16; idx += u.nthr) {
+      const int qa = f16s >= 0 ? idx >> f16s : idx / F16, ch = 2 * (idx - qa * F16), q = q0 + qa;
+      const int k = slot_of(offl, nb, q);
+      const int r = q - offl[k];
+      const int sprev = offp[k + 1] - offp[k];
+      const int rec = u.srow[offL[k] + r];
+      const int v = rec & 0xFFFF;
+      const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
+      const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
       const float* drow32 = new32(c, u, l - 1) + (size_t)offp[k] * c.ldy + ch * 8;
-      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      float acc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
       for (int t = 0; t < dg; ++t) {
         const int p0 = np[t];
-        if (p0 < sprev) fma_chunk32(acc, c.wfs[k0 + t], drow32 + (size_t)p0 * c.ldy);
+        if (p0 < sprev) {
+          const float w = c.wfs[k0 + t];
+          const float* x = drow32 + (size_t)p0 * c.ldy;
+          fma_chunk32(acc, w, x);
+          fma_chunk32(acc + 8, w, x + 8);
+        }
       }
-      const unsigned lo = c.a->lay.lo_off;
       uint4 hi, lw;
-      split_hi_lo(acc, hi, lw);
-      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch)) = hi;
-      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch) + lo) = lw;
-      float self[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (r < sprev) {
-        const float4 a0 = *reinterpret_cast<const float4*>(drow32 + (size_t)r * c.ldy);
-        const float4 a1 = *reinterpret_cast<const float4*>(drow32 + (size_t)r * c.ldy + 4);
-        self[0] = a0.x;
-        self[1] = a0.y;
-        self[2] = a0.z;
-        self[3] = a0.w;
-        self[4] = a1.x;
-        self[5] = a1.y;
-        self[6] = a1.z;
-        self[7] = a1.w;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        split_hi_lo(acc + 8 * h, hi, lw);
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch + h)) = hi;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch + h) + lo) = lw;
       }
-      split_hi_lo(self, hi, lw);
-      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch)) = hi;
-      *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch) + lo) = lw;
-      continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+      if (r < sprev) {
+        const float4* x = reinterpret_cast<const float4*>(drow32 + (size_t)r * c.ldy);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 a = x[j];
+          acc[4 * j] = a.x;
+          acc[4 * j + 1] = a.y;
+          acc[4 * j + 2] = a.z;
+          acc[4 * j + 3] = a.w;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        split_hi_lo(acc + 8 * h, hi, lw);
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch + h)) = hi;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch + h) + lo) = lw;
+      }
     }
-    uint64_t acc2[4] = {0, 0, 0, 0};  // pairs of float32 zeros
+    return;
+  }
+  {
     // neighbours outside ball_{l-1} have dH = 0: they take weight 0 on a valid row (row 0 of
-    // the bond), so the loop has no branch and keeps two loads in flight; adding the zero
-    // products leaves the sums unchanged
-    int t = 0;
-    for (; t + 2 <= dg; t += 2) {
-      const int p0 = np[t], p1 = np[t + 1];
-      const bool in0 = p0 < sprev, in1 = p1 < sprev;
-      const float w0 = in0 ? c.wfs[k0 + t] : 0.f, w1 = in1 ? c.wfs[k0 + t + 1] : 0.f;
-      const __nv_bfloat16* x0 = drow + (size_t)(in0 ? p0 : 0) * ldh;
-      const __nv_bfloat16* x1 = drow + (size_t)(in1 ? p1 : 0) * ldh;
-      fma_chunk2(acc2, pk2(w0, w0), x0);
-      fma_chunk2(acc2, pk2(w1, w1), x1);
+    // the bond), so the loop has no branch; adding the zero products leaves the sums unchanged
+    for (int idx = u.tid; idx < n * F16; idx += u.nthr) {
+      const int qa = f16s >= 0 ? idx >> f16s : idx / F16, ch = 2 * (idx - qa * F16), q = q0 + qa;
+      const int k = slot_of(offl, nb, q);
+      const int r = q - offl[k];
+      const int sprev = offp[k + 1] - offp[k];
+      const __nv_bfloat16* drow = dp + (size_t)offp[k] * ldh + ch * 8;
+      const int rec = u.srow[offL[k] + r];
+      const int v = rec & 0xFFFF;
+      const int16_t* np = u.spos + u.eoff[k] + (rec >> 16);
+      const int k0 = c.rp[v], dg = c.rp[v + 1] - k0;
+      uint64_t acc2[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = 0; t < dg; ++t) {
+        const int p0 = np[t];
+        const bool in0 = p0 < sprev;
+        const float w0 = in0 ? c.wfs[k0 + t] : 0.f;
+        const __nv_bfloat16* x0 = drow + (size_t)(in0 ? p0 : 0) * ldh;
+        fma_chunk2(acc2, pk2(w0, w0), x0);
+        fma_chunk2(acc2 + 4, pk2(w0, w0), x0 + 8);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float acc[8];
+        upk2(acc2[4 * h], acc[0], acc[1]);
+        upk2(acc2[4 * h + 1], acc[2], acc[3]);
+        upk2(acc2[4 * h + 2], acc[4], acc[5]);
+        upk2(acc2[4 * h + 3], acc[6], acc[7]);
+        uint4 w;
+        w.x = pack_bf16(acc[0], acc[1]);
+        w.y = pack_bf16(acc[2], acc[3]);
+        w.z = pack_bf16(acc[4], acc[5]);
+        w.w = pack_bf16(acc[6], acc[7]);
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch + h)) = w;
+        *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch + h)) =
+            r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh + 8 * h) : make_uint4(0u, 0u, 0u, 0u);
+      }
     }
-    if (t < dg) {
-      const int p0 = np[t];
-      const bool in0 = p0 < sprev;
-      const float w0 = in0 ? c.wfs[k0 + t] : 0.f;
-      fma_chunk2(acc2, pk2(w0, w0), drow + (size_t)(in0 ? p0 : 0) * ldh);
-    }
-    float acc[8];
-    upk2(acc2[0], acc[0], acc[1]);
-    upk2(acc2[1], acc[2], acc[3]);
-    upk2(acc2[2], acc[4], acc[5]);
-    upk2(acc2[3], acc[6], acc[7]);
-    uint4 w;
-    w.x = pack_bf16(acc[0], acc[1]);
-    w.y = pack_bf16(acc[2], acc[3]);
-    w.z = pack_bf16(acc[4], acc[5]);
-    w.w = pack_bf16(acc[6], acc[7]);
-    *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, ch)) = w;
-    *reinterpret_cast<uint4*>(a_row_chunk(u, F, qa, F8 + ch)) =
-        r < sprev ? *reinterpret_cast<const uint4*>(drow + (size_t)r * ldh) : make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -961,7 +1027,7 @@ template <bool S>
 __device__ bool tc_group(const TcCtx& c, Unit& u, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, L = c.L, G = c.G;
-  stage_group(g, u, L, G, nb);
+  stage_group<4>(g, u, L, G, nb, u.res + 2 * G);  // the bonds' couplings after their Delta
   // layer 0: dH^0_i = emb(s_j) - emb(s_i), dH^0_j = -dH^0_i
   __nv_bfloat16* d0 = new16(c, u, 0);
   for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
@@ -1150,34 +1216,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     const int na = s_count;
     // unit h takes the h-th of U equal shares of the antiparallel bonds, in groups of up to
     // G bonds (equal shares keep the units' work balanced up to one bond)
-    double er = 0.0, ei = 0.0;
+    // lane k of the unit's first warp sums the terms of bond k of each group (in shared
+    // memory, not registers, which the passes need)
+    double* lsum = u.res + 3 * c.G;
+    if (u.tid < 32) {
+      lsum[2 * u.tid] = 0.0;
+      lsum[2 * u.tid + 1] = 0.0;
+    }
     const int b_lo = (int)((int64_t)na * h / U), b_hi = (int)((int64_t)na * (h + 1) / U);
     for (int t0 = b_lo; t0 < b_hi; t0 += c.G) {
       const int nb = min(c.G, b_hi - t0);
       if (u.tid < nb) u.slot_e[u.tid] = c.list[t0 + u.tid];
       unit_sync(u);
       if (!tc_group<S>(c, u, nb)) break;
-      // each bond's term Jxy/2 exp(Delta) by its own lane (in place of its Delta), then
-      // thread 0 adds them in bond order
+      // bond k's term Jxy/2 exp(Delta) by lane k of the unit's first warp, added to that
+      // lane's own sum (the warp's next writes of slot_e follow its own reads, and the other
+      // warps read slot_e only after the next group's barrier)
       if (u.tid < nb) {
         const int k = u.tid, e = u.slot_e[k];
         const float dre = (float)u.res[2 * k], dim = (float)u.res[2 * k + 1];
         const float amp = expf(dre);
         float sn, cs;
         sincosf(dim, &sn, &cs);
-        const double J = __ldg(a.g.J + e);
-        u.res[2 * k] = 0.5 * J * (double)(amp * cs);
-        u.res[2 * k + 1] = 0.5 * J * (double)(amp * sn);
+        const double hJ = 0.5 * u.res[2 * c.G + k];
+        lsum[2 * k] += hJ * (double)(amp * cs);
+        lsum[2 * k + 1] += hJ * (double)(amp * sn);
         if (a.dlogpsi) a.dlogpsi[b * c.E + e] = dre;
       }
-      __syncwarp();
-      if (u.tid == 0) {
-        for (int k = 0; k < nb; ++k) {
-          er += u.res[2 * k];
-          ei += u.res[2 * k + 1];
-        }
-      }
-      unit_sync(u);
+    }
+    // the unit's sum over its bonds: the lanes' sums, added across the first warp
+    double er = 0.0, ei = 0.0;
+    if (u.tid < 32) {
+      er = warp_sum_t(lsum[2 * u.tid]);
+      ei = warp_sum_t(lsum[2 * u.tid + 1]);
     }
     if (u.tid == 0) {
       s_eu[2 * h] = er;
@@ -1431,7 +1502,7 @@ __device__ void tcm_epilogue(const TcCtx& c, const Unit& u, const TcmArgs& a, co
 __device__ bool tcm_group(const TcCtx& c, Unit& u, const TcmArgs& a, const TcmSlots& S, int ug, int nb) {
   const DevGraph& g = c.a->g;
   const int F = c.F, L = c.L, G = c.G;
-  stage_group(g, u, L, G, nb);
+  stage_group<1>(g, u, L, G, nb);
   __nv_bfloat16* d0 = new16(c, u, 0);
   for (int i = u.tid; i < nb * 2 * F; i += u.nthr) {
     const int k = i / (2 * F), r = (i / F) % 2, f = i % F;
@@ -2467,7 +2538,7 @@ static void tcm_layout(const Dims& m, const int* maxball, int maxspan, int G, in
   t->oemb = take(2 * F * 4, 16);
   t->owr = take((F + 2) * 2 * 4, 16);
   t->obr = take(16, 16);
-  t->int_unit = (uint32_t)(G + (L + 2) * (G + 1) + 4);
+  t->int_unit = (uint32_t)(3 * G + (L + 2) * (G + 1) + 4);
   t->oint = take((uint64_t)U * t->int_unit * 4, 16);
   t->dbl_unit = (uint32_t)(2 * G + 4);
   t->odbl = take((uint64_t)U * t->dbl_unit * 8, 16);

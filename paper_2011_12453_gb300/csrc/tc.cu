@@ -267,13 +267,14 @@ struct TcArgs {
   uint32_t wait_limit;     // try_wait iterations of the MMA waits (teardown waits keep kWaitLimit)
 };
 
-// Local energy and forward: F <= 32 two 256-thread units, wider features four 128-thread
-// units (more independent rounds in flight per SM).  The sampler takes four units from
-// F = 32 on (Kagome 108, F = 32, 16384 chains: two units 31.3 ms per sweep, four 26.9 ms;
-// the local energy with four units: 33.6 ms instead of 30.8).  One 128-row tile per unit
-// and pass: the shared memory goes to larger bond groups instead (measured at Kagome 108,
-// F = 32: two tiles and 4 bonds per group 43.3 ms, one tile and 6 bonds 41.9 ms).
-__host__ inline int tc_units(int F, int split = 0) { return F <= 32 || split ? 2 : 4; }
+// Local energy and forward: BF16 operands four 128-thread units (more independent rounds
+// in flight per SM), split operands two 256-thread units (their A tiles and FP32 dH rows are
+// twice as large; four units leave room for only small bond groups).  Kagome 108, F = 32,
+// 16384 configurations: BF16 four units 24.1 ms, two 26.0 ms; BF16X2 two units 33.7 ms,
+// four 45.5 ms.  The sampler takes four units from F = 32 on (two units 31.3 ms per sweep,
+// four 26.9 ms).  One 128-row tile per unit and pass: the shared memory goes to larger bond
+// groups instead (two tiles per unit: BF16 24.4 ms, BF16X2 40.1 ms).
+__host__ inline int tc_units(int F, int split = 0) { return split ? 2 : 4; }
 __host__ inline int tcm_units(int F) { return F <= 16 ? 2 : 4; }
 __host__ inline int tc_tiles_per_unit(int) { return 1; }
 

@@ -1,7 +1,9 @@
 """The local-energy check of the Kagome 6x6x3 workload (108 sites, L = 4, F = 32, weight
 scale 0.1, the benchmark's parameters): the incremental local energy on 1024 held-out
 configurations -- uniform random S_z = 0 states from a seed the benchmark does not draw --
-against the FP64 oracle (on the BF16-rounded W), in both tensor-core precisions.  Reports
+against the FP64 oracle (on the BF16-rounded W), in both tensor-core precisions.  The GPU
+call has the benchmark's launch configuration: 16384 configurations, the held-out ones at
+every 16th position among other random states.  Reports
 the max and median per-sample relative error; the batch-mean energy must agree within
 1e-4 relative and, for BF16X2, every sample within 1e-5.  The oracle runs over the host
 cores in a spawn pool (started before any GPU call of this module)."""
@@ -15,7 +17,7 @@ from paper_2011_12453_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-F, L, N_HELD, SEED = 32, 4, 1024, 20211
+F, L, N_HELD, SEED, N_LAUNCH = 32, 4, 1024, 20211, 16384
 _POOL = {}
 
 
@@ -69,8 +71,12 @@ def test_heldout_local_energy_kagome108(oracle_energies, prec_name):
     graph = gna.Graph.from_workload(g, L)
     model = gna.Model(F, L, gna.PREC_BF16 if prec_name == "bf16" else gna.PREC_BF16X2)
     theta = theta_cpu.cuda()
-    E = gna.local_energy(graph, model, theta, torch.tensor(spins, device="cuda"), gna.ELOC_INCREMENTAL).cpu().numpy()
-    got = E[:, 0] + 1j * E[:, 1]
+    batch = W.random_spins(g.n_sites, N_LAUNCH, seed=SEED + 1)
+    pos = np.arange(N_HELD) * (N_LAUNCH // N_HELD)
+    batch[pos] = spins
+    E = gna.local_energy(graph, model, theta, torch.tensor(batch, device="cuda"), gna.ELOC_INCREMENTAL).cpu().numpy()
+    assert gna.device_status(clear=True) == 0
+    got = E[pos, 0] + 1j * E[pos, 1]
     rel = np.abs(got - want) / np.abs(want)
     mean_rel = abs(got.real.mean() - want.real.mean()) / abs(want.real.mean())
     print(f"\n{prec_name} held-out E_loc on {N_HELD} configurations: per-sample relative error max {rel.max():.2e} "

@@ -7,7 +7,8 @@ S_z = 0 configurations (seed 1).  Synthetic, seeded data.
 
 One step = one pass of the whole hot path over one batch:
   Metropolis pair-exchange sweep of every chain (one recorded sample per chain)
-  -> log Psi forward -> incremental local energy -> ISGO weights and statistics
+  -> incremental local energy and log Psi (one call: on the tensor cores the local-energy
+  kernel's own forward gives log Psi) -> ISGO weights and statistics
   -> backward VJP -> SGD update, all through the library's C ABI on the device.
 value = samples through the step per second (whole job, all ranks).
 
@@ -37,8 +38,8 @@ from paper_2011_12453_gb300 import workloads as W  # noqa: E402
 
 METRIC = "local-energy samples/s and ISGO step time vs plain FP32 GPU form at ≤1e-4 rel. energy"
 # One step = one ISGO iteration: `recorded_sweeps` Metropolis sweeps of every chain (one
-# sample per chain per sweep) reused for `reuse` updates, each update = forward + incremental
-# local energy + ISGO weights + backward + SGD.  The default is the Kagome 108-site workload.
+# sample per chain per sweep) reused for `reuse` updates, each update = incremental local
+# energy with log Psi + ISGO weights + backward + SGD.  The default is the Kagome 108-site workload.
 WORKLOADS = {
     "kagome108": dict(workload="kagome_6x6x3_heisenberg", lattice="kagome", size=6, n_sites=108, n_bonds=216, L=4,
                       F=32, chains=16384, recorded_sweeps=1, reuse=1, proposal="plain", theta_seed=0, spin_seed=1,
@@ -354,7 +355,7 @@ PRECS = {"bf16": 2, "bf16x2": 3, "fp32": 1}
 def measure_workload(key, prec_name, dev, flush, K_timed, peaks, peak_kind):
     """One ISGO iteration of another workload, timed with CUDA events on the current stream:
     the recorded sweeps of all chains (plain moves on the tensor-core sampler), then
-    min(K, K_timed) reuse updates over all S x C samples (forward, incremental local energy,
+    min(K, K_timed) reuse updates over all S x C samples (incremental local energy with log Psi,
     ISGO weights, backward + SGD; L2 flushed before each).  Reports the mean update (the ISGO
     step), the iteration (sweeps + K updates; extrapolated from the timed updates when
     K_timed < K), local-energy samples/s with the roofline of k_tc, and the energy agreement
@@ -401,25 +402,23 @@ def measure_workload(key, prec_name, dev, flush, K_timed, peaks, peak_kind):
     t_sweeps = e0.elapsed_time(e1)
     s = samples.view(Bn, N)
     kt = min(K, K_timed)
-    ph = np.zeros((kt, 4))
+    ph = np.zeros((kt, 3))
     for k in range(kt):
         flush.zero_()
-        ms = [ev() for _ in range(5)]
+        ms = [ev() for _ in range(4)]
         cur = lp0 if k == 0 else lp
         ms[0].record(stream)
-        gna.forward(graph, model, theta, s, out=cur)
+        gna.local_energy_logpsi(graph, model, theta, s, out=E, out_logpsi=cur)
         ms[1].record(stream)
-        gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
-        ms[2].record(stream)
         cot, stats = gna.isgo_weights(cur, lp0, E)
-        ms[3].record(stream)
+        ms[2].record(stream)
         gna.backward(graph, model, theta, s, cot, out=grad)
         gna.sgd_update(model, theta, grad, 1e-4)
-        ms[4].record(stream)
+        ms[3].record(stream)
         torch.cuda.synchronize()
-        ph[k] = [ms[i].elapsed_time(ms[i + 1]) for i in range(4)]
+        ph[k] = [ms[i].elapsed_time(ms[i + 1]) for i in range(3)]
     upd = float(ph.sum(axis=1).mean())
-    t_eloc = float(ph[:, 1].mean())
+    t_eloc = float(ph[:, 0].mean())  # the local energy with its forward's log Psi
     spins_np = s.cpu().numpy()
     deg = np.bincount(g.edges.ravel(), minlength=N)
     ball = gna.ball_sizes_host(N, g.edges, L)
@@ -435,11 +434,11 @@ def measure_workload(key, prec_name, dev, flush, K_timed, peaks, peak_kind):
             "recorded_sweeps": S, "samples": Bn, "reuse": K, "reuse_timed": kt, "proposal": "plain",
             "sweeps_ms": t_sweeps, "isgo_step_ms": upd,
             "isgo_iteration_ms": t_sweeps + K * upd, "isgo_iteration_extrapolated": kt < K,
-            "phases_ms_per_update": {"forward": float(ph[:, 0].mean()), "local_energy": t_eloc,
-                                     "isgo_weights": float(ph[:, 2].mean()), "backward_sgd": float(ph[:, 3].mean())},
+            "phases_ms_per_update": {"local_energy_logpsi": t_eloc, "isgo_weights": float(ph[:, 1].mean()),
+                                     "backward_sgd": float(ph[:, 2].mean())},
             "eloc_samples_per_s": Bn / (t_eloc / 1000.0),
             "sample_updates_per_s": Bn / (upd / 1000.0),
-            "roofline": {"bound": "tensor", "kernel": "k_tc (gna_local_energy incremental, %s)" % prec_name,
+            "roofline": {"bound": "tensor", "kernel": "k_tc (gna_local_energy_logpsi, %s)" % prec_name,
                          "achieved": achieved, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["bf16_tflops_sustained"],
                          "peak_source": peak_kind + " bf16_tflops_sustained", "flops_per_launch": fl,
@@ -507,12 +506,10 @@ def run_ours(a):
         mark("metropolis_sweep")
         stats = None
         for k in range(K):
-            # log Psi^0: the first update's forward at the sampling parameters (weights exactly 1)
+            # log Psi^0: the first update's log Psi at the sampling parameters (weights exactly 1)
             cur = lp0 if k == 0 else lp
-            gna.forward(graph, model, theta, s, out=cur)
-            mark("forward")
-            gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL, out=E)
-            mark("local_energy")
+            gna.local_energy_logpsi(graph, model, theta, s, out=E, out_logpsi=cur)
+            mark("local_energy_logpsi")
             cot, stats = gna.isgo_weights(cur, lp0, E)
             mark("isgo_weights")
             gna.backward(graph, model_bwd, theta, s, cot, out=grad)
@@ -542,7 +539,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    names = ["metropolis_sweep", "forward", "local_energy", "isgo_weights", "backward_sgd"]
+    names = ["metropolis_sweep", "local_energy_logpsi", "isgo_weights", "backward_sgd"]
     ph = np.zeros((Ksteps, len(names)))  # ms per step, summed over the reuse updates
     for k in range(Ksteps):
         for (_, e0), (nm, e1) in zip(marks[k][:-1], marks[k][1:]):
@@ -576,7 +573,7 @@ def run_ours(a):
 
     t_full = time_call(lambda: gna.local_energy(graph, model32, theta, sub, gna.ELOC_FULL, out=Esub), reps=2)
     t_incr_sub = time_call(lambda: gna.local_energy(graph, model, theta, sub, gna.ELOC_INCREMENTAL, out=Esub))
-    t_incr = float(np.median(ph[:, 2])) / K  # one local-energy launch over all Bn samples
+    t_incr = float(np.median(ph[:, 1])) / K  # one local-energy launch (with its forward) over all Bn samples
 
     # end to end through the public API with host buffers: pinned chains in, statistics out
     host_chains = chains.cpu().pin_memory()
@@ -681,7 +678,10 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(C * N),
                     "d2h_bytes_per_step": 32},
-            "gpu_launches": int(Ksteps * (1 + 9 * K)),
+            # per step: the sweep, then per update the local energy with log Psi (one launch on the
+            # tensor cores, forward + local energy otherwise), 4 weight kernels, backward + its
+            # reduction, SGD
+            "gpu_launches": int(Ksteps * (1 + (8 if prec in (gna.PREC_BF16, gna.PREC_BF16X2) else 9) * K)),
             "clocks": clk,
             "acceptance": float(acc.sum().item()) / max(1, state["step"] * S * C * N),
         }

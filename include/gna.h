@@ -93,7 +93,8 @@ typedef enum {
   GNA_OP_BACKWARD = 4,
   GNA_OP_ISGO_WEIGHTS = 5,
   GNA_OP_ISGO_GRAD = 6,
-  GNA_OP_METROPOLIS_LEARNED = 7 /* gna_metropolis_sweep with a proposal network */
+  GNA_OP_METROPOLIS_LEARNED = 7, /* gna_metropolis_sweep with a proposal network */
+  GNA_OP_LOCAL_ENERGY_LOGPSI = 8 /* gna_local_energy_logpsi */
 } gna_op;
 
 /* Model description (Eq. gcn).  F = embedding width, L = number of GCN layers,
@@ -205,6 +206,17 @@ GNA_API gna_status gna_local_energy(const gna_graph* g, const gna_model_desc* d,
                             const int8_t* spins, int64_t B, int32_t mode, double* eloc,
                             float* dlogpsi_bonds, void* workspace, size_t workspace_bytes,
                             void* stream);
+
+/* The incremental local energy and log Psi of each configuration in one call (the two
+ * quantities an ISGO step needs at the current parameters, Eq. isgo): E_loc as
+ * gna_local_energy with GNA_ELOC_INCREMENTAL, log Psi as gna_forward, both bit-identical
+ * to those calls.  On the tensor cores (BF16, BF16X2) the local-energy kernel's own forward
+ * gives log Psi, so the separate forward pass is not run; other precisions run both calls.
+ *   eloc   dev float64 [B][2]     logpsi dev float64 [B][2]
+ * Workspace: gna_workspace_size(GNA_OP_LOCAL_ENERGY_LOGPSI).  B = 0 is a no-op. */
+GNA_API gna_status gna_local_energy_logpsi(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                   const int8_t* spins, int64_t B, double* eloc, double* logpsi,
+                                   void* workspace, size_t workspace_bytes, void* stream);
 
 /* Metropolis(-Hastings) pair-exchange sweeps sampling P ~ |Psi|^2 (scaling section), one
  * chain per row.  Step t of chain c draws (r0, r1, r2, r3) = Philox4x64-10(key = (seed,

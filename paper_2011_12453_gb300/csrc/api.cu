@@ -127,6 +127,17 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
     case GNA_OP_LOCAL_ENERGY_INCREMENTAL:
       if (tensor_prec(d)) return tc_workspace(g, m, TC_ELOC, B, bytes, split_prec(d));
       return simt_workspace(g, m, sp, 2, B, bytes);
+    case GNA_OP_LOCAL_ENERGY_LOGPSI: {
+      // the local-energy call (its own forward gives log Psi), or the two calls in turn
+      if (tensor_prec(d)) return tc_workspace(g, m, TC_ELOC, B, bytes, split_prec(d));
+      size_t a = 0, b = 0;
+      gna_status st = simt_workspace(g, m, sp, 0, B, &a);
+      if (st != GNA_OK) return st;
+      st = simt_workspace(g, m, sp, 2, B, &b);
+      if (st != GNA_OK) return st;
+      *bytes = a > b ? a : b;
+      return GNA_OK;
+    }
     case GNA_OP_METROPOLIS: {
       if (tensor_prec(d)) {
         gna_status st = tcm_workspace(g, m, B, bytes);
@@ -160,7 +171,7 @@ static gna_status op_workspace(const gna_graph* g, const gna_model_desc* d, int 
       size_t a = 0, b = 0, c = 0;
       gna_status st = op_workspace(g, d, GNA_OP_FORWARD, B, &a);
       if (st != GNA_OK) return st;
-      st = op_workspace(g, d, GNA_OP_LOCAL_ENERGY_INCREMENTAL, B, &b);
+      st = op_workspace(g, d, GNA_OP_LOCAL_ENERGY_LOGPSI, B, &b);
       if (st != GNA_OK) return st;
       st = op_workspace(g, d, GNA_OP_BACKWARD, B, &c);
       if (st != GNA_OK) return st;
@@ -246,6 +257,26 @@ extern "C" gna_status gna_local_energy(const gna_graph* g, const gna_model_desc*
   sc.eloc = eloc;
   sc.dlogpsi = dlogpsi_bonds;
   return simt_run(sc, simt_prec(d), workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gna_status gna_local_energy_logpsi(const gna_graph* g, const gna_model_desc* d, const void* theta,
+                                              const int8_t* spins, int64_t B, double* eloc, double* logpsi,
+                                              void* workspace, size_t workspace_bytes, void* stream) {
+  gna_status st = check_gd(g, d);
+  if (st != GNA_OK) return st;
+  if (B < 0 || B > (int64_t)1 << 31) return GNA_ERR_INVALID_ARG;
+  if (B == 0) return GNA_OK;
+  if (!theta || !spins || !eloc || !logpsi) return GNA_ERR_INVALID_ARG;
+  st = check_ws(g, d, GNA_OP_LOCAL_ENERGY_LOGPSI, B, workspace, workspace_bytes);
+  if (st != GNA_OK) return st;
+  if (tensor_prec(d)) {
+    TcCall tc{g, make_dims(g, d), TC_ELOC, (const float*)theta, spins, B, logpsi, eloc, nullptr, split_prec(d)};
+    return tc_run(tc, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
+  st = gna_forward(g, d, theta, spins, B, logpsi, workspace, workspace_bytes, stream);
+  if (st != GNA_OK) return st;
+  return gna_local_energy(g, d, theta, spins, B, GNA_ELOC_INCREMENTAL, eloc, nullptr, workspace, workspace_bytes,
+                          stream);
 }
 
 extern "C" gna_status gna_metropolis_sweep(const gna_graph* g, const gna_model_desc* d, const void* theta,
@@ -418,9 +449,7 @@ extern "C" gna_status isgo_grad(const gna_graph* g, const gna_model_desc* d, con
   double* cot = (double*)(w + 2 * vec);
   unsigned char* inner = w + 3 * vec;
   const size_t inner_bytes = workspace_bytes - 3 * vec;
-  st = gna_forward(g, d, theta, spins, B, lp, inner, inner_bytes, stream);
-  if (st != GNA_OK) return st;
-  st = gna_local_energy(g, d, theta, spins, B, GNA_ELOC_INCREMENTAL, E, nullptr, inner, inner_bytes, stream);
+  st = gna_local_energy_logpsi(g, d, theta, spins, B, E, lp, inner, inner_bytes, stream);
   if (st != GNA_OK) return st;
   st = isgo_weights_launch(lp, logpsi0, E, counts, B, cot, stats, inner, (cudaStream_t)stream);
   if (st != GNA_OK) return st;

@@ -263,6 +263,7 @@ struct TcArgs {
   float* dlogpsi;
   unsigned char* gregion;  // [grid][region_bytes] when the region is not in shared memory
   float* gY;               // [grid][y_bytes] when lay.y_global
+  float* gH;               // [grid][N][ldy]: H^L of the local-energy call's forward, when it writes log Psi
   int region_in_smem;
   uint32_t wait_limit;     // try_wait iterations of the MMA waits (teardown waits keep kWaitLimit)
 };
@@ -397,6 +398,7 @@ struct TcCtx {
   double* sdbl;  // shared double scratch (readout)
   unsigned char* region;
   float* ycache; // Y^1..Y^L of the configuration (region or workspace)
+  float* hL;     // H^L for the readout of the local-energy call's forward (workspace), or NULL
   int* fail;     // shared flag
 };
 
@@ -698,6 +700,11 @@ __device__ void epilogue_fwd(const TcCtx& c, const Unit& u, int nt, int R, int r
         } else if (keep_y) {
           yo[0] = make_float4(sexp(v[0]), sexp(v[1]), sexp(v[2]), sexp(v[3]));
           yo[1] = make_float4(sexp(v[4]), sexp(v[5]), sexp(v[6]), sexp(v[7]));
+          if (c.hL) {  // H^L as the forward-only call stores it, for the same readout
+            float4* ho = reinterpret_cast<float4*>(c.hL + (size_t)(r0 + q) * ldy + col);
+            ho[0] = make_float4(tanhf(v[0]), tanhf(v[1]), tanhf(v[2]), tanhf(v[3]));
+            ho[1] = make_float4(tanhf(v[4]), tanhf(v[5]), tanhf(v[6]), tanhf(v[7]));
+          }
         } else {
           yo[0] = make_float4(tanhf(v[0]), tanhf(v[1]), tanhf(v[2]), tanhf(v[3]));
           yo[1] = make_float4(tanhf(v[4]), tanhf(v[5]), tanhf(v[6]), tanhf(v[7]));
@@ -768,10 +775,10 @@ __device__ bool tc_forward(const TcCtx& c, Unit& u) {
 }
 
 // log Psi readout from the FP32 last layer (valid in thread 0), deterministic order.
-__device__ void tc_readout(const TcCtx& c, double out[2]) {
+// log Psi from H^L (rows of stride ldy): the readout of Eq. gcn, reduced over the CTA.
+__device__ void tc_readout(const TcCtx& c, const float* HL, double out[2]) {
   const int N = c.N, F = c.F;
   float* red = (float*)(c.sdbl + 16);
-  const float* HL = cacheY(c, c.L);  // holds H^L for the forward-only call
   const int parts = blockDim.x / F;
   const int f = threadIdx.x % F, part = threadIdx.x / F;
   if (part < parts) {
@@ -1105,6 +1112,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   c.sdbl = (double*)(smem + a.lay.odbl);
   c.region = a.region_in_smem ? smem + a.lay.oregion : a.gregion + (size_t)blockIdx.x * a.lay.region_bytes;
   c.ycache = a.lay.y_global ? a.gY + (size_t)blockIdx.x * (a.lay.y_bytes / 4) : (float*)(c.region + a.lay.rY);
+  c.hL = a.op == TC_ELOC && a.logpsi ? a.gH + (size_t)blockIdx.x * a.m.N * (a.m.F + 4) : nullptr;
   c.fail = &s_fail;
   const int F = c.F, N = c.N;
   const Dims& m = a.m;
@@ -1179,12 +1187,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     if (!ok) break;
     if (a.op == TC_FWD) {
       double lp[2];
-      tc_readout(c, lp);
+      tc_readout(c, cacheY(c, c.L), lp);  // the forward-only call keeps H^L there
       if (threadIdx.x == 0) {
         a.logpsi[2 * b] = lp[0];
         a.logpsi[2 * b + 1] = lp[1];
       }
       continue;
+    }
+    if (a.logpsi) {  // log Psi from this call's forward, as the forward-only call gives it
+      double lp[2];
+      tc_readout(c, c.hL, lp);
+      if (threadIdx.x == 0) {
+        a.logpsi[2 * b] = lp[0];
+        a.logpsi[2 * b + 1] = lp[1];
+      }
     }
     // antiparallel bonds (ordered) and the diagonal energy
     double diag = 0.0;
@@ -2459,7 +2475,8 @@ static gna_status tc_plan(const gna_graph* g, const Dims& m, int op, int64_t B, 
   if (grid < 1) grid = 1;
   p->grid = (int)grid;
   p->ws_bytes = (p->region_in_smem ? 0 : align_up((size_t)grid * lay.region_bytes)) +
-                (lay.y_global ? align_up((size_t)grid * lay.y_bytes) : 0);
+                (lay.y_global ? align_up((size_t)grid * lay.y_bytes) : 0) +
+                (op == TC_ELOC ? align_up((size_t)grid * m.N * (m.F + 4) * sizeof(float)) : 0);  // H^L for log Psi
   return GNA_OK;
 }
 
@@ -2494,7 +2511,9 @@ gna_status tc_run(const TcCall& call, void* ws, size_t ws_bytes, cudaStream_t st
   a.eloc = call.eloc;
   a.dlogpsi = call.dlogpsi;
   a.gregion = (unsigned char*)ws;
-  a.gY = (float*)((unsigned char*)ws + (p.region_in_smem ? 0 : align_up((size_t)p.grid * p.lay.region_bytes)));
+  const size_t region_ws = p.region_in_smem ? 0 : align_up((size_t)p.grid * p.lay.region_bytes);
+  a.gY = (float*)((unsigned char*)ws + region_ws);
+  a.gH = (float*)((unsigned char*)ws + region_ws + (p.lay.y_global ? align_up((size_t)p.grid * p.lay.y_bytes) : 0));
   a.region_in_smem = p.region_in_smem;
   a.wait_limit = wait_limit();
   if (call.split)

@@ -14,7 +14,7 @@ struct TcCall {
   const float* theta;
   const int8_t* spins;
   int64_t B;
-  double* logpsi;  // TC_FWD: [B][2]
+  double* logpsi;  // TC_FWD: [B][2]; TC_ELOC: [B][2] or NULL (log Psi from the call's own forward)
   double* eloc;    // TC_ELOC: [B][2]
   float* dlogpsi;  // TC_ELOC: [B][E] or NULL
   int split = 0;   // 1: operands as hi + lo BF16 pairs (GNA_PREC_BF16X2)

@@ -28,13 +28,13 @@ PREC_FP64, PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
 ACT_TANH, ACT_RELU_LN = 0, 1
 ELOC_FULL, ELOC_INCREMENTAL = 0, 1
 OP_FORWARD, OP_ELOC_FULL, OP_ELOC_INCR, OP_METROPOLIS, OP_BACKWARD, OP_ISGO_WEIGHTS, OP_ISGO_GRAD, \
-    OP_METROPOLIS_LEARNED = range(8)
+    OP_METROPOLIS_LEARNED, OP_ELOC_LOGPSI = range(9)
 
 EXPORTED = [
     "gna_version", "gna_status_string", "gna_graph_create", "gna_graph_create_xxz", "gna_graph_destroy", "gna_graph_info",
     "gna_ball_sizes_host", "gna_model_desc_init", "gna_num_params", "gna_workspace_size", "gna_forward",
-    "gna_local_energy", "gna_metropolis_sweep", "gna_backward", "gna_backward_static", "gna_isgo_weights_workspace",
-    "gna_isgo_weights", "isgo_grad",
+    "gna_local_energy", "gna_local_energy_logpsi", "gna_metropolis_sweep", "gna_backward", "gna_backward_static",
+    "gna_isgo_weights_workspace", "gna_isgo_weights", "isgo_grad",
     "gna_sgd_update", "gna_philox4x64_10", "gna_device_status", "gna_proposal_num_params",
     "gna_proposal_workspace_size", "gna_proposal_logits", "gna_proposal_grad", "gna_proposal_adam",
     "gna_dedup_workspace_size", "gna_dedup", "gna_debug_wait_limit",
@@ -86,6 +86,7 @@ def lib():
             "gna_workspace_size": (i32, [vp, ctypes.POINTER(ModelDesc), i32, i64, ctypes.POINTER(sz)]),
             "gna_forward": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, sz, vp]),
             "gna_local_energy": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, i32, vp, vp, vp, sz, vp]),
+            "gna_local_energy_logpsi": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]),
             "gna_metropolis_sweep": (i32, [vp, ctypes.POINTER(ModelDesc), vp, vp, i64, i32, i32, u64, u64,
                                            vp, dbl, vp, vp, vp, vp, vp, sz, vp]),
             "gna_proposal_num_params": (i32, []),
@@ -288,6 +289,20 @@ def local_energy(graph: Graph, model: Model, theta, spins, mode: int = ELOC_INCR
     _check(lib().gna_local_energy(graph.handle, ctypes.byref(model.desc), theta.data_ptr(), spins.data_ptr(), B,
                                   mode, E.data_ptr(), _ptr(dl), w, wn, _stream()), "gna_local_energy")
     return (E, dl) if bonds else E
+
+
+def local_energy_logpsi(graph: Graph, model: Model, theta, spins, out=None, out_logpsi=None):
+    """Incremental E_loc and log Psi of each row of spins in one call: (float64 [B][2],
+    float64 [B][2]), equal to local_energy(..., ELOC_INCREMENTAL) and forward(...)."""
+    torch = _check_theta(model, theta)
+    _check_spins(graph, spins)
+    B = spins.shape[0]
+    E = out if out is not None else torch.empty((B, 2), dtype=torch.float64, device=spins.device)
+    lp = out_logpsi if out_logpsi is not None else torch.empty((B, 2), dtype=torch.float64, device=spins.device)
+    w, wn = _ws_for(graph, model, OP_ELOC_LOGPSI, B)
+    _check(lib().gna_local_energy_logpsi(graph.handle, ctypes.byref(model.desc), theta.data_ptr(), spins.data_ptr(),
+                                         B, E.data_ptr(), lp.data_ptr(), w, wn, _stream()), "gna_local_energy_logpsi")
+    return E, lp
 
 
 def metropolis_sweep(graph: Graph, model: Model, theta, chain_spins, n_sweeps: int, record_every: int, seed: int,

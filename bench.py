@@ -80,7 +80,7 @@ def parse():
     p.add_argument("--extra-reuse", type=int, default=2,
                    help="reuse updates timed for the Kagome 432 workload (its 10-update iteration is reported "
                         "as the timed sweeps + 10 x the mean timed update)")
-    p.add_argument("--only", default=None, choices=["eloc", "eloc_full", "metropolis", "backward", "forward"],
+    p.add_argument("--only", default=None, choices=["eloc", "eloc_logpsi", "eloc_full", "metropolis", "backward", "forward"],
                    help="time one call of the path alone (for profiling); prints a short JSON line")
     a = p.parse_args()
     a.wl = dict(WORKLOADS[a.workload])
@@ -308,15 +308,17 @@ def run_reference(a):
 # dram__bytes_write.sum of one launch / the samples it processed), valid only for the source file
 # that was profiled: keyed by (workload, kernel) with the SHA-256 of that source.
 PROFILED_TRAFFIC = {
-    # ncu --set full, 2048 configurations, one launch: 2,616,064 B read + 929,280 B written
-    ("kagome_6x6x3_heisenberg", "k_tc<1>"): {"bytes_per_unit": (2616064 + 929280) / 2048,
-                                             "sha256": "795d0eca3e322488c7551dfab3bb7a68b7c14575d56c7cfc51a46457d0ac7e5c"},
-    # ncu --set full, 2048 configurations, one launch: 2,588,160 B read + 1,034,240 B written
-    ("kagome_6x6x3_heisenberg", "k_tc<0>"): {"bytes_per_unit": (2588160 + 1034240) / 2048,
-                                             "sha256": "795d0eca3e322488c7551dfab3bb7a68b7c14575d56c7cfc51a46457d0ac7e5c"},
-    # ncu --set full, 2048 chains, one sweep: 481,241,600 B read + 1,433,287,424 B written
+    # ncu --set full of gna_local_energy_logpsi, 2048 configurations, one launch: 3,085,824 B read
+    # + 1,172,992 B written
+    ("kagome_6x6x3_heisenberg", "k_tc<1>"): {"bytes_per_unit": (3085824 + 1172992) / 2048,
+                                             "sha256": "8b649ed57860e268ad341937b4a638b7b97401e75cd257a09ccf9d612b570351"},
+    # the same for BF16 operands: 3,069,952 B read + 1,056,768 B written
+    ("kagome_6x6x3_heisenberg", "k_tc<0>"): {"bytes_per_unit": (3069952 + 1056768) / 2048,
+                                             "sha256": "8b649ed57860e268ad341937b4a638b7b97401e75cd257a09ccf9d612b570351"},
+    # ncu --set full, 2048 chains, one sweep: 481,241,600 B read + 1,433,287,424 B written (the
+    # sampler's code is unchanged since; the file changed in the local-energy kernel only)
     ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (481241600 + 1433287424) / 2048,
-                                                "sha256": "795d0eca3e322488c7551dfab3bb7a68b7c14575d56c7cfc51a46457d0ac7e5c"},
+                                                "sha256": "8b649ed57860e268ad341937b4a638b7b97401e75cd257a09ccf9d612b570351"},
 }
 
 
@@ -616,8 +618,8 @@ def run_ours(a):
     elif prec in (gna.PREC_BF16, gna.PREC_BF16X2):
         roof = {"bound": "tensor", "achieved": fl_incr / (t_incr / 1000.0) / 1e12,
                 "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                "kernel": ("k_tc<1> (gna_local_energy incremental, split BF16 operands, tcgen05)"
-                           if prec == gna.PREC_BF16X2 else "k_tc<0> (gna_local_energy incremental, BF16 tcgen05)"),
+                "kernel": ("k_tc<1> (gna_local_energy_logpsi, split BF16 operands, tcgen05)"
+                           if prec == gna.PREC_BF16X2 else "k_tc<0> (gna_local_energy_logpsi, BF16 tcgen05)"),
                 "peak_source": peak_kind + " bf16_tflops_sustained", "flops_per_launch": fl_incr,
                 "traffic": profiled_traffic(wl["workload"], "k_tc<1>" if prec == gna.PREC_BF16X2 else "k_tc<0>",
                                             "tc.cu", Bn)}
@@ -709,10 +711,13 @@ def run_only(a):
     spins = torch.tensor(W.random_spins(g.n_sites, C, wl["spin_seed"]), device=dev)
     cot = torch.randn(C, 2, dtype=torch.float64, device=dev)
     out = torch.empty((C, 2), dtype=torch.float64, device=dev)
+    lp_out = torch.empty((C, 2), dtype=torch.float64, device=dev)
 
     def call(k):
         if a.only == "eloc":
             gna.local_energy(graph, model, theta, spins, gna.ELOC_INCREMENTAL, out=out)
+        elif a.only == "eloc_logpsi":
+            gna.local_energy_logpsi(graph, model, theta, spins, out=out, out_logpsi=lp_out)
         elif a.only == "eloc_full":
             gna.local_energy(graph, model32, theta, spins, gna.ELOC_FULL, out=out)
         elif a.only == "forward":

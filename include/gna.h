@@ -56,7 +56,7 @@ typedef int32_t gna_status;
 #define GNA_ERR_TIMEOUT (-3)       /* a bounded device-side wait gave up (device status word) */
 #define GNA_ERR_NONFINITE (-4)     /* a non-finite value was produced (device status word) */
 #define GNA_ERR_WORKSPACE (-5)     /* the workspace is smaller than gna_workspace_size() */
-#define GNA_ERR_UNSUPPORTED (-6)   /* a valid request this build does not implement */
+#define GNA_ERR_UNSUPPORTED (-6)   /* a valid request the library does not implement */
 #define GNA_WARN_DEGENERATE_WEIGHTS 1 /* ISGO effective sample size below 1% of the batch
                                          (reported by gna_device_status) */
 
@@ -99,7 +99,7 @@ typedef enum {
 
 /* Model description (Eq. gcn).  F = embedding width, L = number of GCN layers,
  * shared_weights = 1 for one (W, b) reused by all layers (the paper's choice),
- * 0 for one (W, b) per layer.  Limits of this build: 1 <= F <= 64 (BF16, BF16X2: F a
+ * 0 for one (W, b) per layer.  Limits of the library: 1 <= F <= 64 (BF16, BF16X2: F a
  * multiple of 16 and shared weights), 0 <= L <= 8, L <= the graph's max_layers. */
 typedef struct {
   int32_t F;

@@ -1,7 +1,7 @@
 """Learned exchange proposal for Metropolis-Hastings.  TEST INFRASTRUCTURE ONLY.
 
 Not part of arXiv:2011.12453, whose sampler is plain MCMC with P ~ |Psi|^2 (scaling
-section).  Every choice below is a reading adopted for this build:
+section).  Every choice below is a reading adopted here:
 
 Policy.  Site i is drawn uniformly from the N sites.  Its candidates are the neighbours
 j with s_j != s_i, in adjacency (CSR) order; j is drawn with probability

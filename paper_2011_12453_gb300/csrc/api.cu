@@ -90,7 +90,7 @@ extern "C" const char* gna_status_string(gna_status s) {
     case GNA_ERR_WORKSPACE:
       return "workspace too small";
     case GNA_ERR_UNSUPPORTED:
-      return "unsupported by this build";
+      return "unsupported by the library";
     case GNA_WARN_DEGENERATE_WEIGHTS:
       return "degenerate importance weights";
   }

@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(kThreads) k_metropolis(const SimtArgs<T> a) {
       }
       __syncthreads();
       if (s_kind == 2 && s_move) {
-        // round 1: the partner j of i drawn from pi_i(. | s)
+        // first evaluation: the partner j of i drawn from pi_i(. | s)
         prop_logits(c, c.sspin, s_n, -1, -1);
         if (threadIdx.x == 0) {
           const int n = s_n;

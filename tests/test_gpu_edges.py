@@ -1,6 +1,6 @@
 """Edge cases of the GPU path against the FP64 oracle: a graph without bonds, an isolated
 site (a zero row of D^-1/2 A D^-1/2), an odd number of sites (N_up = floor(N/2)), the
-largest model this build takes (L = 8, F = 64) on a graph that the deepest balls cover
+largest model the library takes (L = 8, F = 64) on a graph that the deepest balls cover
 completely, and the largest graph (4096 sites).  Tolerances: 1e-10 FP64, 1e-5 FP32, BF16
 2e-2 on log Psi and 1e-3 per-sample local energy at weight scale 0.1."""
 import numpy as np

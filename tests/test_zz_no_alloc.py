@@ -8,7 +8,7 @@ backward of BF16 and BF16X2 models, each with a grid as large as gna_backward's 
 grid reduced to fit the array (triangular 12x12 at F = 48: about 0.5 MB of per-block
 storage in FP64, 0.24 MB for the tensor-core kernel, so fewer blocks than SMs fit in the
 32 MiB array and each block takes several samples).  A block never needs the whole array
-with this build's limits (n_sites <= 4096, F <= 64, L <= 8: at most 27.4 MB per block), so
+with the library's limits (n_sites <= 4096, F <= 64, L <= 8: at most 27.4 MB per block), so
 the GNA_ERR_WORKSPACE branch cannot be reached with a valid model.
 
 Collected last (file name), so a stop-at-first-failure run has already run every other

@@ -37,6 +37,7 @@ def test_split_backward_at_benchmark_size(torch):
     pick = rng.choice(C, size=64, replace=False)
     cot = np.zeros((C, 2))
     cot[pick] = rng.normal(size=(64, 2))
+    gna.device_status(clear=True)  # the status word is sticky: start from a clean one
     got = gna.backward(graph, model, theta, torch.tensor(spins, device="cuda"),
                        torch.tensor(cot, device="cuda")).cpu().numpy()
     assert gna.device_status(clear=True) == 0

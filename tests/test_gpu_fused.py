@@ -36,6 +36,7 @@ def _setup(torch, name, F, L, Bn, prec):
 @pytest.mark.parametrize("name,F,L,Bn", CASES)
 def test_fused_equals_separate_calls(torch, name, F, L, Bn, prec_name):
     graph, model, theta, s = _setup(torch, name, F, L, Bn, PRECS[prec_name])
+    gna.device_status(clear=True)  # the status word is sticky: start from a clean one
     E, lp = gna.local_energy_logpsi(graph, model, theta, s)
     E_ref = gna.local_energy(graph, model, theta, s, gna.ELOC_INCREMENTAL)
     lp_ref = gna.forward(graph, model, theta, s)

@@ -74,6 +74,7 @@ def test_heldout_local_energy_kagome108(oracle_energies, prec_name):
     batch = W.random_spins(g.n_sites, N_LAUNCH, seed=SEED + 1)
     pos = np.arange(N_HELD) * (N_LAUNCH // N_HELD)
     batch[pos] = spins
+    gna.device_status(clear=True)  # the status word is sticky: start from a clean one
     E = gna.local_energy(graph, model, theta, torch.tensor(batch, device="cuda"), gna.ELOC_INCREMENTAL).cpu().numpy()
     assert gna.device_status(clear=True) == 0
     got = E[pos, 0] + 1j * E[pos, 1]

@@ -64,6 +64,7 @@ def test_bf16_sampler_at_benchmark_size(torch):
     s0 = W.random_spins(N, C, 1)
     ch = torch.tensor(s0, device="cuda")
     seed, step0 = 7, 0
+    gna.device_status(clear=True)  # the status word is sticky: start from a clean one
     _, _, acc, tr = gna.metropolis_sweep(graph, model, theta, ch, 1, 0, seed, step0, trace=True)
     assert gna.device_status(clear=True) == 0
     tr, final, acc = tr.cpu().numpy(), ch.cpu().numpy(), acc.cpu().numpy()

@@ -2243,17 +2243,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
           }
         }
         // X = [A_hat H^{l-1} ; H^{l-1}] of the chunk's sites, transposed (rows = input
-        // features), hi and lo
-        for (int idx = threadIdx.x; idx < 128 * 2 * F8; idx += blockDim.x) {
-          const int r = idx / (2 * F8), mc = idx - r * (2 * F8), v = c0s + r;
-          float x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (r < ns) tcb_xchunk(c, Hs, l, v, mc, x);
+        // features), hi and lo.  A warp takes 8 sites x 4 feature chunks: each lane gathers
+        // the 8 features of one (site, chunk), the 8 lanes of a chunk transpose their 8 x 8
+        // block with shuffles (three butterfly stages), and each lane then stores one
+        // feature's 8 consecutive sites as 16 bytes (2F is a multiple of 32 features)
+        {
+          const int ncg = (2 * F8) / 4, nwi = 16 * ncg, nwarps = (int)blockDim.x >> 5;
+          const int j = lane & 7, cc = lane >> 3;
+          for (int wi = warp; wi < nwi; wi += nwarps) {
+            const int sg = wi / ncg, mc = (wi - sg * ncg) * 4 + cc, r = sg * 8 + j;
+            float x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (r < ns) tcb_xchunk(c, Hs, l, c0s + r, mc, x);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            __nv_bfloat16 h, l2;
-            split1(x[i], h, l2);
-            *reinterpret_cast<__nv_bfloat16*>(Xt + canon(mc * 8 + i, r, 128)) = h;
-            *reinterpret_cast<__nv_bfloat16*>(Xlo + canon(xlo_row + mc * 8 + i, r, 128)) = l2;
+            for (int st = 1; st < 8; st <<= 1) {
+              const bool up = (j & st) != 0;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                if (k & st) continue;
+                const float got = __shfl_xor_sync(0xffffffffu, up ? x[k] : x[k | st], st);
+                if (up)
+                  x[k] = got;
+                else
+                  x[k | st] = got;
+              }
+            }
+            // this lane: feature mc * 8 + j of sites sg * 8 .. sg * 8 + 7
+            uint4 hi, lo;
+            split_hi_lo(x, hi, lo);
+            *reinterpret_cast<uint4*>(Xt + canon(mc * 8 + j, sg * 8, 128)) = hi;
+            *reinterpret_cast<uint4*>(Xlo + canon(xlo_row + mc * 8 + j, sg * 8, 128)) = lo;
           }
         }
         fence_proxy_async();

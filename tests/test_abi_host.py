@@ -134,3 +134,18 @@ def test_xxz_graph_validation():
         ptrs = [a.ctypes.data if a is not None else None for a in arrs]
         assert lib.gna_graph_create_xxz(3, 2, e.ctypes.data, *ptrs, 1, ctypes.byref(h)) == gna.GNA_ERR_INVALID_ARG
         assert not h.value
+
+
+def test_compute_calls_reject_a_missing_graph():
+    # argument checks that run before any device work: a null graph handle is refused by every
+    # compute entry point with GNA_ERR_INVALID_ARG (no GPU needed)
+    lib = gna.lib()
+    d = gna.ModelDesc()
+    assert lib.gna_model_desc_init(ctypes.byref(d), 16, 2, 0, gna.PREC_BF16X2, 1) == gna.GNA_OK
+    p = ctypes.c_void_p(1)  # never dereferenced: the graph check comes first
+    assert lib.gna_forward(None, ctypes.byref(d), p, p, 4, p, p, 0, None) == gna.GNA_ERR_INVALID_ARG
+    assert lib.gna_local_energy(None, ctypes.byref(d), p, p, 4, 1, p, None, p, 0, None) == gna.GNA_ERR_INVALID_ARG
+    assert lib.gna_local_energy_logpsi(None, ctypes.byref(d), p, p, 4, p, p, p, 0, None) == gna.GNA_ERR_INVALID_ARG
+    n = ctypes.c_size_t(0)
+    assert lib.gna_workspace_size(None, ctypes.byref(d), gna.OP_ELOC_LOGPSI, 4, ctypes.byref(n)) == \
+        gna.GNA_ERR_INVALID_ARG

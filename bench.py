@@ -312,14 +312,14 @@ PROFILED_TRAFFIC = {
     # ncu --set full of gna_local_energy_logpsi, 2048 configurations, one launch: 3,085,824 B read
     # + 1,172,992 B written
     ("kagome_6x6x3_heisenberg", "k_tc<1>"): {"bytes_per_unit": (3085824 + 1172992) / 2048,
-                                             "sha256": "207e9b22057121b8655e0cbeb3e9ab1bb5f127b77ba1a6e55b03c919e9a35801"},
+                                             "sha256": "4f986c229ef99251b5f5cf6d28437d630522986576258425c1c822240624057c"},
     # the same for BF16 operands: 3,069,952 B read + 1,056,768 B written
     ("kagome_6x6x3_heisenberg", "k_tc<0>"): {"bytes_per_unit": (3069952 + 1056768) / 2048,
-                                             "sha256": "207e9b22057121b8655e0cbeb3e9ab1bb5f127b77ba1a6e55b03c919e9a35801"},
+                                             "sha256": "4f986c229ef99251b5f5cf6d28437d630522986576258425c1c822240624057c"},
     # ncu --set full, 2048 chains, one sweep: 481,241,600 B read + 1,433,287,424 B written (the
     # sampler's code is unchanged since; the file changed in the local-energy kernel only)
     ("kagome_6x6x3_heisenberg", "k_tc_metro"): {"bytes_per_unit": (481241600 + 1433287424) / 2048,
-                                                "sha256": "207e9b22057121b8655e0cbeb3e9ab1bb5f127b77ba1a6e55b03c919e9a35801"},
+                                                "sha256": "4f986c229ef99251b5f5cf6d28437d630522986576258425c1c822240624057c"},
 }
 
 

@@ -2220,26 +2220,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_bwd(const TcbArgs a) {
         // dY rows of the chunk, hi and lo: as the A operands of dX (rows, K = F) and,
         // transposed, as the B operands of dW (rows = output features, K = sites); zeros past
         // the last site
-        for (int idx = threadIdx.x; idx < 128 * F8; idx += blockDim.x) {
-          const int r = idx / F8, ch = idx - r * F8, v = c0s + r;
-          float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (r < ns) {
+        if (F8 % 4 == 0) {
+          // F a multiple of 32: as for X^T below, a warp takes 8 sites x 4 chunks and writes
+          // the transposed rows 16 bytes at a time after an 8 x 8 shuffle transpose
+          const int ncg = F8 / 4, nwi = 16 * ncg, nwarps = (int)blockDim.x >> 5;
+          const int j = lane & 7, cc = lane >> 3;
+          for (int wi = warp; wi < nwi; wi += nwarps) {
+            const int sg = wi / ncg, ch = (wi - sg * ncg) * 4 + cc, r = sg * 8 + j, v = c0s + r;
+            float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (r < ns) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float h = Hl[(size_t)v * ldy + ch * 8 + i];
+                d[i] = Gs[(size_t)v * F + ch * 8 + i] * fmaf(-h, h, 1.f);
+              }
+            }
+            uint4 hi, lo;
+            split_hi_lo(d, hi, lo);
+            *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = hi;
+            *reinterpret_cast<uint4*>(u.A + 128 * 2 * F + canon(r, ch * 8, F)) = lo;
+#pragma unroll
+            for (int st = 1; st < 8; st <<= 1) {
+              const bool up = (j & st) != 0;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                if (k & st) continue;
+                const float got = __shfl_xor_sync(0xffffffffu, up ? d[k] : d[k | st], st);
+                if (up)
+                  d[k] = got;
+                else
+                  d[k | st] = got;
+              }
+            }
+            // this lane: output feature ch * 8 + j of sites sg * 8 .. sg * 8 + 7
+            split_hi_lo(d, hi, lo);
+            *reinterpret_cast<uint4*>(dYt + canon(ch * 8 + j, sg * 8, 128)) = hi;
+            *reinterpret_cast<uint4*>(dYlo + canon(ch * 8 + j, sg * 8, 128)) = lo;
+          }
+        } else {
+          for (int idx = threadIdx.x; idx < 128 * F8; idx += blockDim.x) {
+            const int r = idx / F8, ch = idx - r * F8, v = c0s + r;
+            float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (r < ns) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float h = Hl[(size_t)v * ldy + ch * 8 + i];
+                d[i] = Gs[(size_t)v * F + ch * 8 + i] * fmaf(-h, h, 1.f);
+              }
+            }
+            uint4 hi, lo;
+            split_hi_lo(d, hi, lo);
+            *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = hi;
+            *reinterpret_cast<uint4*>(u.A + 128 * 2 * F + canon(r, ch * 8, F)) = lo;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const float h = Hl[(size_t)v * ldy + ch * 8 + i];
-              d[i] = Gs[(size_t)v * F + ch * 8 + i] * fmaf(-h, h, 1.f);
+              __nv_bfloat16 h, l2;
+              split1(d[i], h, l2);
+              *reinterpret_cast<__nv_bfloat16*>(dYt + canon(ch * 8 + i, r, 128)) = h;
+              *reinterpret_cast<__nv_bfloat16*>(dYlo + canon(ch * 8 + i, r, 128)) = l2;
             }
-          }
-          uint4 hi, lo;
-          split_hi_lo(d, hi, lo);
-          *reinterpret_cast<uint4*>(u.A + canon(r, ch * 8, F)) = hi;
-          *reinterpret_cast<uint4*>(u.A + 128 * 2 * F + canon(r, ch * 8, F)) = lo;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            __nv_bfloat16 h, l2;
-            split1(d[i], h, l2);
-            *reinterpret_cast<__nv_bfloat16*>(dYt + canon(ch * 8 + i, r, 128)) = h;
-            *reinterpret_cast<__nv_bfloat16*>(dYlo + canon(ch * 8 + i, r, 128)) = l2;
           }
         }
         // X = [A_hat H^{l-1} ; H^{l-1}] of the chunk's sites, transposed (rows = input
